@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of Sparse Frequent Directions on one GB300 (or N, one process each).
+
+Workload (one step = one whole stream sketched, every hot-path stage run):
+  n = 1,000,000 rows, d = 50,000, l = 100, nnz/row ~ Poisson(50), columns
+  Zipf(1.1) without repeats, planted rank-20 signal (10 * 0.8^t) + 0.1 N(0,1),
+  fp32 values / int32 indices, seed = rank. 20 buffers of 50,000 rows each go
+  through BoostedSparseShrink (SimultaneousIteration with q = 13, VerifySpectral)
+  and DenseShrink. The CSR stream (~400 MB) is larger than L2, so successive
+  steps start cold.
+
+Metric: input nnz/s (whole job, all ranks). `value` times the device-resident
+stream (`sfd_append_rows` with device pointers + `sfd_sketch`); `e2e` times the
+same call sequence from pinned host buffers (host->device copy of the stream
+and device->host copy of the sketch inside the timed region).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+stream (the first 10,000 rows: one flushed buffer through BSSh + DSh).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="c2", n=1_000_000, d=50_000, ell=100, k=20, mu=50, zipf=1.1, rank=20,
+                scale=10.0, decay=0.8, noise=0.1)
+DESC = ("SFD stream n=1,000,000 d=50,000 l=100, nnz/row~Poisson(50), Zipf(1.1) columns, "
+        "planted rank-20 (10*0.8^t) + 0.1 N(0,1), fp32 CSR")
+METRIC = "SFD input nnz/sec at fixed cov-error"
+REF_SAMPLE_ROWS = 10_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", type=int, default=WORKLOAD["n"], help="stream length (default: full)")
+    ap.add_argument("--no-check", action="store_true", help="skip the cov-err evaluation")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_stream(rows, seed):
+    from paper_1602_00412_gb300 import synth
+    w = WORKLOAD
+    return synth.planted(rows, w["d"], w["mu"], w["zipf"], w["rank"], w["scale"], w["decay"],
+                         w["noise"], seed, name="c2")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- checks
+def cov_err_check(X, B, k):
+    """cov-err = ||A^T A - B^T B||_2 / ||A||_F^2 and the FD bound ||A - A_k||_F^2/(l - k)
+    (Sec. 5 measures; evaluated with scipy on the host)."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+    A = X.to_scipy()
+    Bd = B.astype(np.float64)
+    d = A.shape[1]
+
+    def mv(x):
+        x = np.asarray(x).reshape(-1)
+        return A.T @ (A @ x) - Bd.T @ (Bd @ x)
+    op = spla.LinearOperator((d, d), matvec=mv, dtype=np.float64)
+    lam = spla.eigsh(op, k=1, which="LA", tol=1e-6, return_eigenvectors=False)[0]
+    lo = spla.eigsh(op, k=1, which="SA", tol=1e-6, return_eigenvectors=False)[0]
+    fro2 = float(A.multiply(A).sum())
+    s = spla.svds(A, k=k, tol=1e-6, return_singular_vectors=False)
+    tail = fro2 - float((s ** 2).sum())
+    ell = B.shape[0]
+    return {"cov_err": float(max(abs(lam), abs(lo)) / fro2), "cov_norm": float(max(abs(lam), abs(lo))),
+            "fd_bound": float(tail / (ell - k)), "min_eig_rel": float(lo / fro2), "k": k}
+
+
+# ------------------------------------------------------------ cpu baseline
+def run_oracle_sample(rows, seed, threads):
+    """Time the FP64 oracle on the first `rows` rows of the stream in a fresh
+    process (spawned, BLAS limited to `threads`). Returns (seconds, nnz)."""
+    code = (
+        "import sys,time,json; sys.path.insert(0,%r)\n"
+        "import bench\n"
+        "from oracle import sfd as O\n"
+        "X = bench.make_stream(%d, %d)\n"
+        "t=time.perf_counter(); O.sfd_stream(X.indptr,X.indices,X.values,%d,%d,%d)\n"
+        "print(json.dumps({'sec': time.perf_counter()-t, 'nnz': X.nnz}))\n"
+    ) % (ROOT, rows, seed, WORKLOAD["d"], WORKLOAD["ell"], seed)
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["sec"], out["nnz"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """dram bytes per launch of the SpMM kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "spmm_c2_traffic.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1602_00412_gb300", "csrc", "k_sparse.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return j.get("bytes_per_launch") if j.get("source_sha") == h else None
+
+
+# ------------------------------------------------------------------ arms
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    times, nnz = [], 0
+    for i in range(args.warmup + args.steps):
+        sec, nnz = run_oracle_sample(REF_SAMPLE_ROWS, 0, threads)
+        if i >= args.warmup:
+            times.append(sec)
+    tot = sum(times)
+    val = nnz * len(times) / tot
+    sample = "first %d rows of the c2 stream (%d nnz): one flushed buffer, BSSh + DSh in FP64" % (
+        REF_SAMPLE_ROWS, nnz)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "nnz/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": DESC, "sample_rows": REF_SAMPLE_ROWS},
+            "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    from paper_1602_00412_gb300.build import build
+    build()
+    from paper_1602_00412_gb300 import sfd
+
+    X = make_stream(args.rows, rank)
+    w = WORKLOAD
+    d, ell = w["d"], w["ell"]
+    stream = torch.cuda.current_stream()
+    # device-resident inputs
+    ip_d = torch.from_numpy(X.indptr).cuda()
+    ix_d = torch.from_numpy(X.indices).cuda()
+    vv_d = torch.from_numpy(X.values).cuda()
+    B_d = torch.empty((ell, d), device="cuda")
+    # pinned host inputs for e2e
+    ip_h = torch.from_numpy(X.indptr).pin_memory().numpy()
+    ix_h = torch.from_numpy(X.indices).pin_memory().numpy()
+    vv_h = torch.from_numpy(X.values).pin_memory().numpy()
+    B_h = torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()
+    ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1)
+
+    def step_device():
+        ctx.reset()
+        ctx.append(ip_d, ix_d, vv_d)
+        ctx.sketch(B_d)
+
+    def step_host():
+        ctx.reset()
+        ctx.append(ip_h, ix_h, vv_h)
+        ctx.sketch(B_h)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step_device()
+    clk = ClockSampler(local)
+    clk.start()
+    ms = timed(step_device, args.steps)
+    # counters cover the last timed step (every step starts with a reset)
+    st = ctx.stats()
+    clocks = clk.stop()
+    spmm_launches, spmm_ms, spmm_bytes = st["spmm_launches"], st["spmm_ms"], st["spmm_bytes"]
+    for _ in range(max(1, args.warmup // 3)):
+        step_host()
+    ms_e2e = timed(step_host, args.steps)
+    B = B_d.cpu().numpy()
+    nnz_all = X.nnz * world
+    value = nnz_all * args.steps / (ms / 1e3)
+    e2e = nnz_all * args.steps / (ms_e2e / 1e3)
+    peak, peak_kind = peaks()
+    per_launch_bytes = spmm_bytes / max(1, spmm_launches)
+    per_launch_s = spmm_ms / 1e3 / max(1, spmm_launches)
+    achieved = per_launch_bytes / per_launch_s / 1e9 if spmm_launches else None
+    out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": DESC, "rows": X.n, "d": d, "ell": ell, "nnz_per_rank": X.nnz,
+                      "buffers_per_step": st["buffers"], "attempts_per_step": st["attempts"],
+                      "q_per_attempt": st["q_total"] / max(1, st["attempts"]),
+                      "l2": "inputs larger than L2 (CSR stream %.0f MB per rank)" % (
+                          (X.indptr.nbytes + X.indices.nbytes + X.values.nbytes) / 1e6),
+                      "parallelism": "independent streams per GPU (weak)" if world > 1 else "1 GPU"},
+           "rows_per_s": X.n * world * args.steps / (ms / 1e3),
+           "e2e": {"value": e2e, "unit": "nnz/s",
+                   "h2d_bytes_per_step": int(X.indptr.nbytes + X.indices.nbytes + X.values.nbytes),
+                   "d2h_bytes_per_step": int(B_h.nbytes)},
+           "roofline": {"kernel": "k_spmm (A'X via CSR, A'^T Y via CSC, incl. split fix-up)",
+                        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": (achieved / peak) if achieved else None,
+                        "peak_kind": "of %s" % peak_kind,
+                        "traffic": traffic_record(), "launches_per_step": spmm_launches,
+                        "algorithmic_bytes_per_launch": per_launch_bytes,
+                        "avg_launch_us": per_launch_s * 1e6},
+           "gpu_launches": int(st["kernel_launches"]) * args.steps,
+           "gpu_launches_per_step": int(st["kernel_launches"]),
+           "clocks": clocks}
+    if rank == 0 and not args.no_check:
+        out["accuracy"] = cov_err_check(X, B, w["k"])
+        out["accuracy"]["within_fd_bound"] = out["accuracy"]["cov_norm"] <= out["accuracy"]["fd_bound"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        sec, nnz = run_oracle_sample(REF_SAMPLE_ROWS, 0, threads)
+        out["cpu_baseline"] = {"value": nnz / sec, "unit": "nnz/s", "cores": threads,
+                               "kind": "oracle",
+                               "sample": "first %d rows (%d nnz) of the stream: one flushed "
+                                         "buffer through BSSh + DSh, FP64 numpy/scipy" % (
+                                             REF_SAMPLE_ROWS, nnz)}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        ours_arm(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

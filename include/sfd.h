@@ -1,0 +1,194 @@
+/*
+ * sfd.h - C ABI of the GB300 Sparse Frequent Directions library (libsfd.so).
+ *
+ * Sparse Frequent Directions (Ghashami, Liberty, Phillips): rows of a sparse
+ * matrix A (n x d) arrive one at a time (Sec. 1, the row-streaming model);
+ * the library keeps an l x d sketch B with O(d l) memory (Fact in Sec. 4.2).
+ * Rows are buffered until the buffer A' holds l*d non-zeros or d rows
+ * (Alg. 2); then B' = BoostedSparseShrink(A') (Alg. 4: SparseShrink of Alg. 3
+ * on top of SimultaneousIteration of Alg. 1, checked by VerifySpectral of
+ * Alg. 6) and B = DenseShrink([B; B']) (Alg. 5). Sketches are mergeable
+ * (Sec. 3.1): merge(B1, B2) = DenseShrink([B1; B2]).
+ *
+ * Conventions for every entry point
+ *  - Return value: SFD_OK (0) or one of the SFD_E* codes below. No C++
+ *    exception crosses this boundary. After SFD_EINVAL the context is
+ *    unchanged and usable; after SFD_ECUDA / SFD_ETIMEOUT it must be destroyed.
+ *  - `where` says where caller arrays live: SFD_HOST (0) or SFD_DEVICE (1,
+ *    memory of the current CUDA device). Caller arrays stay the caller's; the
+ *    library copies what it keeps before the call returns.
+ *  - Dense matrices are row-major float32 with the leading dimension stated.
+ *  - A context is bound to the CUDA device current at sfd_create and runs on
+ *    one CUDA stream (options.cuda_stream, or a stream it creates). Calls on
+ *    one context must not overlap; distinct contexts are independent.
+ *  - Every call returns with its work finished on the device (results
+ *    written, stream synchronised), except where stated.
+ */
+#ifndef SFD_H
+#define SFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFD_ABI_VERSION 1u
+
+#define SFD_OK 0
+#define SFD_EINVAL 1   /* bad argument: l < 1, l > d, index outside [0,d), non-monotone indptr, NaN/Inf value, ... */
+#define SFD_ENOMEM 2   /* device or host allocation failed */
+#define SFD_ECUDA 3    /* CUDA runtime error (message in sfd_last_error) */
+#define SFD_EVERIFY 4  /* strict mode: a buffer stayed unverified after retry_cap attempts */
+#define SFD_ETIMEOUT 5 /* a bounded device-side wait ran out */
+
+#define SFD_HOST 0
+#define SFD_DEVICE 1
+
+typedef struct sfd_ctx sfd_ctx; /* opaque, library-owned */
+
+/* Options. Initialise with sfd_options_init(), then change fields. */
+typedef struct sfd_options {
+  uint32_t abi_version; /* must be SFD_ABI_VERSION */
+  double delta;         /* failure probability delta of Alg. 4 / Theorem 4.1 (default 0.01) */
+  int32_t verify;       /* 1: BoostedSparseShrink with VerifySpectral (Alg. 4, default);
+                           0: SparseShrink called directly, as in the paper's experiments (Sec. 5) */
+  double c_q;           /* power count q = ceil(c_q * ln(m/eps)/eps), eps = 1/4 (Alg. 1 with the
+                           eps of Alg. 3); default 0.25, i.e. q = ceil(ln(4m)) */
+  int32_t q_override;   /* >= 0: use this q for every buffer; -1 (default): the schedule above */
+  int32_t retry_cap;    /* SparseShrink attempts per buffer before it is kept unverified (default 8) */
+  int32_t precision;    /* 0: plain fp32 (default); 1: mixed, tensor-core dense stages */
+  int32_t q_mode;       /* 0: fixed schedule (default); 1: learned predictor set by sfd_set_q_model */
+  int32_t strict;       /* 1: a buffer left unverified makes sfd_append_rows return SFD_EVERIFY */
+  int32_t inject_vs_fail; /* testing: force this many VerifySpectral verdicts to False (host-side) */
+  void* cuda_stream;    /* cudaStream_t to run on; NULL: the context creates its own */
+  int32_t profile;      /* 1: time every sparse-product launch with CUDA events (sfd_stats.spmm_*) */
+} sfd_options;
+
+/* Counters of a context (Alg. 2 / Alg. 4 bookkeeping). */
+typedef struct sfd_stats {
+  int64_t rows_seen;    /* rows appended */
+  int64_t nnz_seen;     /* entries appended */
+  int64_t buffers;      /* buffers closed (SparseShrink path or small-buffer DenseShrink) */
+  int64_t attempts;     /* SparseShrink runs (>= verified buffers) */
+  int64_t vs_rejects;   /* VerifySpectral verdicts that were False */
+  int64_t unverified;   /* buffers kept after retry_cap failed attempts */
+  int64_t q_total;      /* sum of q over all SparseShrink runs */
+  int64_t pending_rows; /* rows in the open buffer */
+  int64_t pending_nnz;  /* entries in the open buffer */
+  double last_delta;    /* Delta of the last accepted buffer (Alg. 4) */
+  double last_logsum;   /* log ||C^p x|| of the last VerifySpectral call */
+  double last_fro2;     /* ||A'||_F^2 of the last buffer */
+  int64_t kernel_launches; /* CUDA kernels this context launched */
+  int64_t spmm_launches;   /* profile: sparse x dense products timed (A' X and A'^T Y) */
+  double spmm_ms;          /* profile: their summed device time (CUDA events, ms) */
+  double spmm_bytes;       /* profile: their algorithmic bytes: entries (8 B each) + row
+                              pointers + dense input + dense output, fp32 */
+} sfd_stats;
+
+/* Per-buffer result of sfd_bssh_buffer. */
+typedef struct sfd_shrink_info {
+  int32_t q;            /* power count used */
+  int32_t attempts;     /* SparseShrink runs */
+  int32_t verified;     /* 1 if VerifySpectral accepted (or verify == 0) */
+  int32_t vs_steps;     /* power steps p of the last VerifySpectral */
+  double delta_shrink;  /* Delta = (||A'||_F^2 - ||B'||_F^2) / (alpha l), alpha = 6/41 */
+  double logsum;        /* log ||C^p x|| of the last VerifySpectral */
+  double fro2_a;        /* ||A'||_F^2 */
+  double fro2_b;        /* ||B'||_F^2 */
+} sfd_shrink_info;
+
+/* Fill `opt` with the defaults listed above. */
+void sfd_options_init(sfd_options* opt);
+
+/* Create a context for rows of dimension d and sketch size l (1 <= l <= d),
+ * Alg. 2 initial state B = 0^{l x d}, empty buffer. `seed` keys every random
+ * draw: G of Alg. 1 and x of Alg. 6 use Philox4x64-10 with
+ * counter (block, buffer index, attempt, tag). opt may be NULL (defaults).
+ * All device memory of the context is allocated here (O(d l) dense plus a
+ * buffer of at most l*d + d entries). Errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA. */
+int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sfd_ctx** out);
+
+/* Append `nrows` rows given in CSR form (Alg. 2 loop body, one row at a time):
+ *   indptr  nrows+1 int64, non-decreasing; row i holds entries
+ *           [indptr[i], indptr[i+1]) of indices/values (indptr[0] may be != 0)
+ *   indices int32 column indices in [0, d); duplicates within a row are summed
+ *   values  float32, finite
+ * All three arrays live in `where` memory. A row may hold at most d entries.
+ * Every full buffer met on the way is shrunk and merged into B before the call
+ * returns. The whole call is validated first: on SFD_EINVAL nothing of it is
+ * applied. SFD_EVERIFY only in strict mode (the rows are applied). */
+int sfd_append_rows(sfd_ctx* ctx, int64_t nrows, const int64_t* indptr, const int32_t* indices,
+                    const float* values, int where);
+
+/* Write the sketch B (l x d, row-major, leading dimension d) to B_out in
+ * `where` memory. Rows still in the open buffer are flushed first: with at
+ * least l rows they take BoostedSparseShrink + DenseShrink, with fewer
+ * DenseShrink([B; A']) (Alg. 2 returns B without them; this closes the stream
+ * the same way at any point). Rows of B are orthogonal; the last is zero. */
+int sfd_sketch(sfd_ctx* ctx, float* B_out, int where);
+
+/* Mergeability (Sec. 3.1): dst.B <- DenseShrink([dst.B; src.B]), after both
+ * open buffers are flushed as in sfd_sketch. src keeps its (flushed) sketch.
+ * Requires equal d and l and the same device. */
+int sfd_merge(sfd_ctx* dst, sfd_ctx* src);
+
+/* Counters; see sfd_stats. */
+int sfd_get_stats(const sfd_ctx* ctx, sfd_stats* out);
+
+/* Start a new stream on the same context: B = 0, the open buffer is dropped,
+ * the buffer counter (and so every Philox key) restarts at 0, counters are
+ * cleared. Device memory is kept. */
+int sfd_reset(sfd_ctx* ctx);
+
+/* Release every resource of the context (NULL is a no-op). */
+void sfd_destroy(sfd_ctx* ctx);
+
+/* Static text for a status code. */
+const char* sfd_strerror(int status);
+
+/* Text of the last error seen by this context ("" if none). */
+const char* sfd_last_error(const sfd_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * One buffer / one stack (the per-step calls used to check each stage).
+ * Device pointers only; the stream is the default stream of the calling
+ * thread's current device. Each call allocates its own scratch.
+ * ------------------------------------------------------------------------ */
+
+/* BoostedSparseShrink (Alg. 4) of one buffer A' (m x d CSR with int32
+ * rowptr[m+1] starting at 0, colidx[nnz], vals[nnz], device memory), with the
+ * randomness of buffer index b under `seed` (same keys as a context).
+ * l <= m is required (Alg. 3). Output Bp_out: l x d row-major (device), the
+ * shrunk sketch B' = Lambda~ V^T. info may be NULL. opt may be NULL. */
+int sfd_bssh_buffer(int64_t m, int64_t d, int32_t ell, const int32_t* rowptr, const int32_t* colidx,
+                    const float* vals, uint64_t seed, int64_t b, const sfd_options* opt,
+                    float* Bp_out, sfd_shrink_info* info);
+
+/* DenseShrink (Alg. 5) of a rows x d matrix M (row-major, device), rows <= 2*l
+ * and l <= 256: B_out (l x d, device) = sqrt(Lambda^2 - lambda_l^2) V^T. */
+int sfd_dense_shrink(int64_t rows, int64_t d, int32_t ell, const float* M, float* B_out);
+
+/* Sparse x dense product of Alg. 1: Y = A X (transpose = 0) or Y = A^T X
+ * (transpose = 1) for A (m x d CSR as in sfd_bssh_buffer), X (d x k or m x k,
+ * leading dimension ldx), Y (m x k or d x k, leading dimension ldy), k <= 256,
+ * ldx, ldy multiples of 4 and >= k, all device memory. */
+int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* colidx,
+                 const float* vals, int32_t k, const float* X, int32_t ldx, float* Y, int32_t ldy,
+                 int32_t transpose);
+
+/* Orthonormalise the columns of X (rows x k, leading dimension ld, device) in
+ * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */
+int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
+
+/* Symmetric eigendecomposition used by Alg. 3 / Alg. 5: the `nwant` largest
+ * eigenvalues (descending, evals[nwant]) and their eigenvectors (evecs,
+ * n x nwant row-major) of the symmetric n x n matrix S (row-major), n <= 512,
+ * all device memory. */
+int sfd_symeig(int32_t n, const float* S, int32_t nwant, float* evals, float* evecs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFD_H */

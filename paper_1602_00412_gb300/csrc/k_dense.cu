@@ -1,0 +1,403 @@
+// Dense kernels of the SparseShrink / DenseShrink path:
+//  - Philox4x64-10 Gaussian draws (G of Alg. 1, x of Alg. 6)
+//  - Gram X^T X of tall-skinny blocks (CholeskyQR of Alg. 1's GramSchmidt,
+//    P P^T of Alg. 3, [B; B'][B; B']^T of Alg. 5)
+//  - tall-skinny products X * T (apply R^-1, H diag(s), U_l diag(s))
+//  - Cholesky of a shifted Gram and the inverse of its factor (one CTA)
+//  - shrink weights sqrt(1 - lambda_l^2 / lambda_i^2) (Alg. 3 / Alg. 5)
+// All arithmetic is fp32; the small k x k factorisations live in one CTA.
+#include <algorithm>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+
+namespace {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon et al., SC'11): 64x64->128 multiplies with the two
+// published multipliers, key bumped by the two Weyl constants each round.
+__device__ __forceinline__ void philox_round(uint64_t& x0, uint64_t& x1, uint64_t& x2, uint64_t& x3,
+                                             uint64_t k0, uint64_t k1) {
+  const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+  uint64_t p0_lo = m0 * x0, p0_hi = __umul64hi(m0, x0);
+  uint64_t p1_lo = m1 * x2, p1_hi = __umul64hi(m1, x2);
+  uint64_t n0 = p1_hi ^ x1 ^ k0;
+  uint64_t n2 = p0_hi ^ x3 ^ k1;
+  x0 = n0; x1 = p1_lo; x2 = n2; x3 = p0_lo;
+}
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t key0, uint64_t key1) {
+  uint64_t k0 = key0, k1 = key1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c[0], c[1], c[2], c[3], k0, k1);
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+
+__device__ __forceinline__ float u24(uint64_t w) {
+  return ((float)(uint32_t)(w >> 40) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+}
+
+__global__ void k_gauss_fill(float* __restrict__ out, int64_t rows, int cols, int ld, uint64_t seed,
+                             uint64_t b, uint64_t r, uint64_t tag) {
+  int64_t blk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t count = rows * (int64_t)cols;
+  if (blk * 4 >= count) return;
+  uint64_t c[4] = {(uint64_t)blk, b, r, tag};
+  philox4x64_10(c, seed, 0ull);
+  float z[4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float ua = u24(c[2 * h]), ub = u24(c[2 * h + 1]);
+    float rad = sqrtf(-2.f * logf(ua));
+    float sn, cs;
+    sincospif(2.f * ub, &sn, &cs);
+    z[2 * h] = rad * cs;
+    z[2 * h + 1] = rad * sn;
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    int64_t e = blk * 4 + t;
+    if (e < count) {
+      int64_t row = e / cols;
+      int col = (int)(e - row * cols);
+      out[row * ld + col] = z[t];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Gram
+constexpr int kT = 64;   // output tile
+constexpr int kR = 32;   // rows per smem stage
+
+__global__ void __launch_bounds__(256)
+    k_gram_tiles(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
+                 int64_t rows_per_chunk, int ntiles, int npairs, float* __restrict__ partial) {
+  __shared__ __align__(16) float As[kR][kT];
+  __shared__ __align__(16) float Bs[kR][kT];
+  const int tp = blockIdx.y, chunk = blockIdx.x;
+  // (ti, tj), ti <= tj, from the row-major index over the upper triangle of tiles
+  int ti = 0, start = 0;
+  while (start + (ntiles - ti) <= tp) { start += ntiles - ti; ++ti; }
+  const int tj = ti + (tp - start);
+  const int n = map.total();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  int64_t r_beg = (int64_t)chunk * rows_per_chunk;
+  int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  for (int64_t r0 = r_beg; r0 < r_end; r0 += kR) {
+#pragma unroll
+    for (int q = 0; q < (kR * kT) / 256; ++q) {
+      int li = threadIdx.x + q * 256;
+      int rr = li / kT, cc = li % kT;
+      int64_t g = r0 + rr;
+      int ca = ti * kT + cc, cb = tj * kT + cc;
+      As[rr][cc] = (g < r_end && ca < n) ? X[g * ldx + map.col(ca)] : 0.f;
+      Bs[rr][cc] = (g < r_end && cb < n) ? X[g * ldx + map.col(cb)] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kR; ++rr) {
+      float4 a = *reinterpret_cast<const float4*>(&As[rr][ty * 4]);
+      float4 bv = *reinterpret_cast<const float4*>(&Bs[rr][tx * 4]);
+      float av[4] = {a.x, a.y, a.z, a.w}, bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* out = partial + ((int64_t)chunk * npairs + tp) * (kT * kT);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(&out[(ty * 4 + i) * kT + tx * 4]) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+}
+
+__global__ void k_gram_reduce(const float* __restrict__ partial, int nchunks, int npairs,
+                              int ntiles, int n, float* __restrict__ G) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  int a = i, c = j;
+  if (a / kT > c / kT) { int t = a; a = c; c = t; }   // use the upper tile (ti <= tj)
+  int ti = a / kT, tj = c / kT;
+  // pair index of (ti, tj), ti <= tj, row-major over the upper triangle of tiles
+  int tp = ti * ntiles - ti * (ti - 1) / 2 + (tj - ti);
+  int off = (a % kT) * kT + (c % kT);
+  float s = 0.f;
+  for (int ch = 0; ch < nchunks; ++ch) s += partial[((int64_t)ch * npairs + tp) * (kT * kT) + off];
+  G[e] = s;
+}
+
+// ---------------------------------------------------------------- X * T
+__global__ void __launch_bounds__(256)
+    k_gemm_ts(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
+              const float* __restrict__ T, int kout, float* __restrict__ Y, int ldy) {
+  __shared__ float Xs[kT][kR + 1];
+  __shared__ __align__(16) float Ts[kR][kT];
+  const int n = map.total();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * kT;
+  const int col0 = blockIdx.y * kT;
+  float acc[4][4] = {};
+  for (int c0 = 0; c0 < n; c0 += kR) {
+#pragma unroll
+    for (int q = 0; q < (kT * kR) / 256; ++q) {
+      int li = threadIdx.x + q * 256;
+      int rr = li / kR, cc = li % kR;
+      int64_t g = row0 + rr;
+      int c = c0 + cc;
+      Xs[rr][cc] = (g < rows && c < n) ? X[g * ldx + map.col(c)] : 0.f;
+      int tr = li / kT, tc = li % kT;
+      int cr = c0 + tr, oc = col0 + tc;
+      Ts[tr][tc] = (cr < n && oc < kout) ? T[(int64_t)cr * kout + oc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int cc = 0; cc < kR; ++cc) {
+      float4 t4 = *reinterpret_cast<const float4*>(&Ts[cc][tx * 4]);
+      float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float xv = Xs[ty * 4 + i][cc];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv, tv[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t g = row0 + ty * 4 + i;
+    if (g >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int oc = col0 + tx * 4 + j;
+      if (oc < kout) Y[g * ldy + oc] = acc[i][j];
+    }
+  }
+}
+
+// --------------------------------------------------- Cholesky + inverse
+__device__ float block_sum_f(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// One CTA of 1024 threads. A (k x lda, lda odd) in shared memory or in the
+// global scratch `gA`. G + s I = L L^T with s = 2^-20 * trace(G) / k, then
+// L^-1 in place, then Rinv = L^-T (upper) written row-major k x k.
+__global__ void __launch_bounds__(1024)
+    k_chol_inv(const float* __restrict__ G, int k, float* __restrict__ Rinv,
+               float* __restrict__ gA, int* __restrict__ flags, int use_smem) {
+  extern __shared__ float sh[];
+  __shared__ float red[33];
+  __shared__ float temp_col[kMaxEll];
+  const int lda = k | 1;
+  float* A = use_smem ? sh : gA;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  float tr = 0.f;
+  for (int e = tid; e < k * k; e += nt) {
+    int i = e / k, j = e % k;
+    float v = G[e];
+    A[i * lda + j] = v;
+    if (i == j) tr += v;
+  }
+  tr = block_sum_f(tr, red);
+  const float shift = tr > 0.f ? ldexpf(tr / (float)k, -20) : 1e-30f;
+  for (int i = tid; i < k; i += nt) A[i * lda + i] += shift;
+  __syncthreads();
+  // right-looking Cholesky, lower triangle
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      float p = A[j * lda + j];
+      if (!(p > 0.f)) {
+        p = shift;
+        atomicAdd(&flags[1], 1);
+      }
+      A[j * lda + j] = sqrtf(p);
+    }
+    __syncthreads();
+    const float ljj = A[j * lda + j];
+    for (int i = j + 1 + tid; i < k; i += nt) A[i * lda + j] /= ljj;
+    __syncthreads();
+    for (int i = j + 1 + warp; i < k; i += nw) {
+      const float lij = A[i * lda + j];
+      for (int t = j + 1 + lane; t <= i; t += 32) A[i * lda + t] -= lij * A[t * lda + j];
+    }
+    __syncthreads();
+  }
+  // L^-1 in place, last column first: Linv[i][j] = -Linv[j][j] * sum_{t=j+1..i} Linv[i][t] L[t][j]
+  for (int j = k - 1; j >= 0; --j) {
+    if (tid == 0) A[j * lda + j] = 1.f / A[j * lda + j];
+    __syncthreads();
+    for (int i = j + 1 + warp; i < k; i += nw) {
+      float s = 0.f;
+      for (int t = j + 1 + lane; t <= i; t += 32) s = fmaf(A[i * lda + t], A[t * lda + j], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) temp_col[i] = s;
+    }
+    __syncthreads();
+    const float dj = A[j * lda + j];
+    for (int i = j + 1 + tid; i < k; i += nt) A[i * lda + j] = -dj * temp_col[i];
+    __syncthreads();
+  }
+  // Rinv = L^-T : Rinv[r][c] = Linv[c][r] for c >= r
+  for (int e = tid; e < k * k; e += nt) {
+    int r = e / k, c = e % k;
+    Rinv[e] = c >= r ? A[c * lda + r] : 0.f;
+  }
+}
+
+// ------------------------------------------------------- shrink weights
+__global__ void k_shrink_weights(const float* __restrict__ evals, const float* __restrict__ evecs,
+                                 int n, int nwant, int nkeep, int thr_zero,
+                                 float* __restrict__ T, double* __restrict__ scal) {
+  __shared__ float s[kMaxEig];
+  const float thr = thr_zero ? 0.f : fmaxf(evals[nkeep - 1], 0.f);
+  for (int j = threadIdx.x; j < nkeep; j += blockDim.x) {
+    float ev = evals[j];
+    s[j] = (ev > thr && ev > 0.f) ? sqrtf(1.f - thr / ev) : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * nkeep; e += blockDim.x) {
+    int i = e / nkeep, j = e % nkeep;
+    T[e] = evecs[i * nwant + j] * s[j];
+  }
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int j = 0; j < nkeep; ++j) acc += fmax((double)evals[j] - (double)thr, 0.0);
+    scal[0] = acc;
+    scal[1] = thr;
+  }
+}
+
+// --------------------------------------------------------------- transpose
+__global__ void k_transpose(const float* __restrict__ in, int64_t rows, int cols, int ld_in,
+                            float* __restrict__ out, int64_t ld_out) {
+  __shared__ float t[32][33];
+  int64_t r0 = (int64_t)blockIdx.x * 32;
+  int c0 = blockIdx.y * 32;
+  int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    int64_t r = r0 + k;
+    int c = c0 + tx;
+    t[k][tx] = (r < rows && c < cols) ? in[r * ld_in + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    int c = c0 + k;
+    int64_t r = r0 + tx;
+    if (c < cols && r < rows) out[(int64_t)c * ld_out + r] = t[tx][k];
+  }
+}
+
+__global__ void k_csr_to_dense_t(const int* __restrict__ ptr, const int* __restrict__ idx,
+                                 const float* __restrict__ val, int rows, float* __restrict__ out,
+                                 int ld) {
+  int r = blockIdx.x;
+  if (r >= rows) return;
+  for (int p = ptr[r] + threadIdx.x; p < ptr[r + 1]; p += blockDim.x)
+    atomicAdd(&out[(int64_t)idx[p] * ld + r], val[p]);
+}
+
+}  // namespace
+
+// ======================================================================= API
+void launch_gauss_fill(float* out, int64_t rows, int cols, int ld, uint64_t seed, uint64_t b,
+                       uint64_t r, uint64_t tag, cudaStream_t s) {
+  int64_t nblk = (rows * cols + 3) / 4;
+  if (nblk == 0) return;
+  k_gauss_fill<<<(unsigned)((nblk + 255) / 256), 256, 0, s>>>(out, rows, cols, ld, seed, b, r, tag);
+  SFD_LAUNCH_CHECK();
+}
+
+void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
+          cudaStream_t s) {
+  const int n = map.total();
+  const int ntiles = (n + kT - 1) / kT;
+  const int npairs = ntiles * (ntiles + 1) / 2;
+  int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kR - 1) / kR, 640 / npairs));
+  int64_t rpc = (rows + nchunks - 1) / nchunks;
+  rpc = ((rpc + kR - 1) / kR) * kR;
+  nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
+  float* partial = ws.gram_partial;
+  if (rows > 0) {
+    dim3 grid(nchunks, npairs);
+    k_gram_tiles<<<grid, 256, 0, s>>>(X, ldx, map, rows, rpc, ntiles, npairs, partial);
+    SFD_LAUNCH_CHECK();
+  } else {
+    nchunks = 0;
+  }
+  int64_t ne = (int64_t)n * n;
+  k_gram_reduce<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(partial, nchunks, npairs, ntiles, n, G);
+  SFD_LAUNCH_CHECK();
+}
+
+void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout, float* Y,
+             int ldy, cudaStream_t s) {
+  if (rows <= 0 || kout <= 0) return;
+  dim3 grid((unsigned)((rows + kT - 1) / kT), (kout + kT - 1) / kT);
+  k_gemm_ts<<<grid, 256, 0, s>>>(X, ldx, map, rows, T, kout, Y, ldy);
+  SFD_LAUNCH_CHECK();
+}
+
+void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s) {
+  const int lda = k | 1;
+  size_t bytes = (size_t)k * lda * sizeof(float);
+  int use_smem = bytes <= 200 * 1024;
+  static unsigned attr_set = 0;  // one bit per device
+  int dev = 0;
+  SFD_CUDA(cudaGetDevice(&dev));
+  if (dev < 32 && !(attr_set & (1u << dev))) {
+    SFD_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set |= 1u << dev;
+  }
+  k_chol_inv<<<1, 1024, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags, use_smem);
+  SFD_LAUNCH_CHECK();
+}
+
+void shrink_weights(const float* evals, const float* evecs, int n, int nwant, int nkeep,
+                    int thr_zero, float* T, double* scal, cudaStream_t s) {
+  k_shrink_weights<<<1, 1024, 0, s>>>(evals, evecs, n, nwant, nkeep, thr_zero, T, scal);
+  SFD_LAUNCH_CHECK();
+}
+
+void transpose(const float* in, int64_t rows, int cols, int ld_in, float* out, int64_t ld_out,
+               cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  dim3 grid((unsigned)((rows + 31) / 32), (cols + 31) / 32);
+  k_transpose<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, ld_in, out, ld_out);
+  SFD_LAUNCH_CHECK();
+}
+
+void csr_to_dense_t(const int* ptr, const int* idx, const float* val, int rows, int64_t d,
+                    float* out, int ld, cudaStream_t s) {
+  (void)d;
+  if (rows <= 0) return;
+  k_csr_to_dense_t<<<rows, 128, 0, s>>>(ptr, idx, val, rows, out, ld);
+  SFD_LAUNCH_CHECK();
+}
+
+}  // namespace sfd

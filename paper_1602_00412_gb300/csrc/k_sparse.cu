@@ -1,0 +1,541 @@
+// Sparse kernels of the SparseShrink hot path (Alg. 1-3 of Ghashami, Liberty,
+// Phillips): buffer validation and ||A'||_F^2, the CSC copy of the buffer
+// (stable LSD radix sort by column, so each column lists rows in ascending
+// order and every result is deterministic), and the sparse x dense products
+// A' X and A'^T Y of SimultaneousIteration / VerifySpectral.
+//
+// Both products run on one segmented kernel: the CSR copy (segments = rows)
+// gives A' X, the CSC copy (segments = columns) gives A'^T Y. Work items cover
+// at most kSplit entries, so the Zipf-heavy head columns of the CSC are cut
+// into many items; their partial rows are summed in a fixed order by a second
+// small kernel (no atomics, bit-reproducible).
+#include <algorithm>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+
+namespace {
+
+constexpr int kScanChunk = 4096;   // elements per block in the scans
+constexpr int kRadixWarps = 16;
+constexpr int kRadixItems = 8;     // per lane
+constexpr int kRadixTile = kRadixWarps * 32 * kRadixItems;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ row ids
+__global__ void k_row_ids(const int* __restrict__ ptr, int nseg, int* __restrict__ rows) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= nseg) return;
+  int b = ptr[warp], e = ptr[warp + 1];
+  for (int i = b + lane; i < e; i += 32) rows[i] = warp;
+}
+
+// ------------------------------------------------------------ check + norms
+constexpr int kCheckBlocks = 1024;
+
+__global__ void k_check_entries(const int* __restrict__ idx, const float* __restrict__ val,
+                                int64_t nnz, int d, int* __restrict__ col_count,
+                                double* __restrict__ block_fro2, int* __restrict__ flags) {
+  float acc = 0.f;
+  int bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = idx[i];
+    float v = val[i];
+    if (c < 0 || c >= d || !isfinite(v)) {
+      bad = 1;
+      continue;
+    }
+    atomicAdd(&col_count[c], 1);
+    acc = fmaf(v, v, acc);
+  }
+  if (bad) atomicOr(&flags[0], 1);
+  __shared__ float red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) block_fro2[blockIdx.x] = (double)v;
+  }
+}
+
+__global__ void k_sum_doubles(const double* __restrict__ in, int n, double* __restrict__ out) {
+  // single block, fixed order: thread t sums t, t+bs, ...; then a tree in shared memory
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += in[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// -------------------------------------------------------------------- scans
+__global__ void k_scan_block_sums(const int* __restrict__ in, int n, int* __restrict__ sums) {
+  int base = blockIdx.x * kScanChunk;
+  int a = 0;
+  for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x) {
+    int g = base + i;
+    if (g < n) a += in[g];
+  }
+  __shared__ int red[32];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = v;
+  }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim a multiple of 32).
+__device__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int ws[32];
+  __shared__ int wtot;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+    int s = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s - t;
+    if (lane == 31) wtot = s;
+  }
+  __syncthreads();
+  int excl = ws[w] + x - v;
+  if (total) *total = wtot;
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ sums, int nb) {
+  // exclusive scan of nb <= 1024 * 8 block sums in place
+  int carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < nb ? sums[i] : 0;
+    int tot;
+    int e = block_exclusive_scan(v, &tot);
+    if (i < nb) sums[i] = carry + e;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_final(const int* __restrict__ in, int n,
+                                                     const int* __restrict__ sums,
+                                                     int* __restrict__ out) {
+  int base = blockIdx.x * kScanChunk;
+  int carry = sums[blockIdx.x];
+  constexpr int per = kScanChunk / 1024;
+  int v[per];
+  int loc = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    int g = base + threadIdx.x * per + j;
+    v[j] = g < n ? in[g] : 0;
+    loc += v[j];
+  }
+  int tot;
+  int e = block_exclusive_scan(loc, &tot);
+  int run = carry + e;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    int g = base + threadIdx.x * per + j;
+    if (g < n) out[g] = run;
+    run += v[j];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = carry + tot;
+}
+
+// ------------------------------------------------------------- radix sort
+__global__ void __launch_bounds__(kRadixWarps * 32)
+    k_radix_hist(const int* __restrict__ key, int64_t n, int shift, int ntiles,
+                 int* __restrict__ hist) {
+  __shared__ int cnt[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int i = threadIdx.x; i < kRadixTile; i += blockDim.x) {
+    int64_t g = base + i;
+    if (g < n) atomicAdd(&cnt[(key[g] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i * ntiles + blockIdx.x] = cnt[i];
+}
+
+__global__ void __launch_bounds__(kRadixWarps * 32)
+    k_radix_scatter(const int* __restrict__ key, const int* __restrict__ a,
+                    const float* __restrict__ b, int64_t n, int shift, int ntiles,
+                    const int* __restrict__ offs, int* __restrict__ key_o, int* __restrict__ a_o,
+                    float* __restrict__ b_o) {
+  __shared__ int wcount[kRadixWarps][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = lane; i < 256; i += 32) wcount[w][i] = 0;
+  __syncwarp();
+  int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * 32 * kRadixItems;
+  int kk[kRadixItems], aa[kRadixItems], dg[kRadixItems], pos[kRadixItems];
+  float bb[kRadixItems];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    int64_t g = base + j * 32 + lane;
+    bool ok = g < n;
+    kk[j] = ok ? key[g] : 0;
+    aa[j] = ok ? a[g] : 0;
+    bb[j] = ok ? b[g] : 0.f;
+    int digit = ok ? ((kk[j] >> shift) & 255) : 256;
+    dg[j] = digit;
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    int rank = __popc(peers & lt);
+    int leader = __ffs(peers) - 1;
+    int basec = digit < 256 ? wcount[w][digit] : 0;
+    pos[j] = basec + rank;
+    __syncwarp();
+    if (lane == leader && digit < 256) wcount[w][digit] = basec + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    int run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kRadixWarps; ++ww) {
+      int c = wcount[ww][threadIdx.x];
+      wcount[ww][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    if (dg[j] < 256) {
+      int dst = offs[dg[j] * ntiles + blockIdx.x] + wcount[w][dg[j]] + pos[j];
+      key_o[dst] = kk[j];
+      a_o[dst] = aa[j];
+      b_o[dst] = bb[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------ work lists
+__global__ void k_count_items(const int* __restrict__ ptr, int nseg, int* __restrict__ n_items,
+                              int* __restrict__ n_slots, int* __restrict__ n_splitflag) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  int len = ptr[s + 1] - ptr[s];
+  int k = len <= kSplit ? 1 : (len + kSplit - 1) / kSplit;
+  n_items[s] = k;
+  n_slots[s] = k > 1 ? k : 0;
+  n_splitflag[s] = k > 1 ? 1 : 0;
+}
+
+__global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* __restrict__ item_off,
+                             const int* __restrict__ slot_off, const int* __restrict__ split_off,
+                             int2* __restrict__ items, int* __restrict__ item_slot,
+                             int* __restrict__ split_seg, int* __restrict__ split_first,
+                             int* __restrict__ split_count) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  int b = ptr[s];
+  int k = item_off[s + 1] - item_off[s];
+  int o = item_off[s];
+  for (int t = 0; t < k; ++t) {
+    items[o + t] = make_int2(s, b + t * kSplit);
+    item_slot[o + t] = k > 1 ? slot_off[s] + t : -1;
+  }
+  if (k > 1) {
+    int q = split_off[s];
+    split_seg[q] = s;
+    split_first[q] = slot_off[s];
+    split_count[q] = k;
+  }
+}
+
+// -------------------------------------------------------------- SpMM (k<=256)
+// One warp per work item; lane l owns float4 columns l, l+32 (VPL of them).
+template <int VPL>
+__global__ void __launch_bounds__(256)
+    k_spmm(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
+           const int2* __restrict__ items, const int* __restrict__ item_slot, int n_items,
+           const float4* __restrict__ X, int ldx4, int nvec, float4* __restrict__ Y, int ldy4,
+           float4* __restrict__ partial) {
+  int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (item >= n_items) return;
+  int2 it = items[item];
+  int seg = it.x, beg = it.y;
+  int end = min(beg + kSplit, ptr[seg + 1]);
+  float4 acc[VPL];
+#pragma unroll
+  for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int p = beg; p < end; p += 32) {
+    int cnt = min(32, end - p);
+    int c_l = lane < cnt ? idx[p + lane] : 0;
+    float v_l = lane < cnt ? val[p + lane] : 0.f;
+    int jj = 0;
+    for (; jj + 4 <= cnt; jj += 4) {
+      int c0 = __shfl_sync(0xffffffffu, c_l, jj);
+      int c1 = __shfl_sync(0xffffffffu, c_l, jj + 1);
+      int c2 = __shfl_sync(0xffffffffu, c_l, jj + 2);
+      int c3 = __shfl_sync(0xffffffffu, c_l, jj + 3);
+      float v0 = __shfl_sync(0xffffffffu, v_l, jj);
+      float v1 = __shfl_sync(0xffffffffu, v_l, jj + 1);
+      float v2 = __shfl_sync(0xffffffffu, v_l, jj + 2);
+      float v3 = __shfl_sync(0xffffffffu, v_l, jj + 3);
+#pragma unroll
+      for (int q = 0; q < VPL; ++q) {
+        int vi = lane + 32 * q;
+        if (vi < nvec) {
+          float4 x0 = __ldg(&X[(int64_t)c0 * ldx4 + vi]);
+          float4 x1 = __ldg(&X[(int64_t)c1 * ldx4 + vi]);
+          float4 x2 = __ldg(&X[(int64_t)c2 * ldx4 + vi]);
+          float4 x3 = __ldg(&X[(int64_t)c3 * ldx4 + vi]);
+          acc[q].x = fmaf(v0, x0.x, acc[q].x); acc[q].y = fmaf(v0, x0.y, acc[q].y);
+          acc[q].z = fmaf(v0, x0.z, acc[q].z); acc[q].w = fmaf(v0, x0.w, acc[q].w);
+          acc[q].x = fmaf(v1, x1.x, acc[q].x); acc[q].y = fmaf(v1, x1.y, acc[q].y);
+          acc[q].z = fmaf(v1, x1.z, acc[q].z); acc[q].w = fmaf(v1, x1.w, acc[q].w);
+          acc[q].x = fmaf(v2, x2.x, acc[q].x); acc[q].y = fmaf(v2, x2.y, acc[q].y);
+          acc[q].z = fmaf(v2, x2.z, acc[q].z); acc[q].w = fmaf(v2, x2.w, acc[q].w);
+          acc[q].x = fmaf(v3, x3.x, acc[q].x); acc[q].y = fmaf(v3, x3.y, acc[q].y);
+          acc[q].z = fmaf(v3, x3.z, acc[q].z); acc[q].w = fmaf(v3, x3.w, acc[q].w);
+        }
+      }
+    }
+    for (; jj < cnt; ++jj) {
+      int c0 = __shfl_sync(0xffffffffu, c_l, jj);
+      float v0 = __shfl_sync(0xffffffffu, v_l, jj);
+#pragma unroll
+      for (int q = 0; q < VPL; ++q) {
+        int vi = lane + 32 * q;
+        if (vi < nvec) {
+          float4 x0 = __ldg(&X[(int64_t)c0 * ldx4 + vi]);
+          acc[q].x = fmaf(v0, x0.x, acc[q].x); acc[q].y = fmaf(v0, x0.y, acc[q].y);
+          acc[q].z = fmaf(v0, x0.z, acc[q].z); acc[q].w = fmaf(v0, x0.w, acc[q].w);
+        }
+      }
+    }
+  }
+  int slot = item_slot[item];
+  float4* out = slot < 0 ? Y + (int64_t)seg * ldy4 : partial + (int64_t)slot * ldy4;
+#pragma unroll
+  for (int q = 0; q < VPL; ++q) {
+    int vi = lane + 32 * q;
+    if (vi < nvec) out[vi] = acc[q];
+  }
+}
+
+template <int VPL>
+__global__ void k_spmm_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
+                             const int* __restrict__ split_count, int n_split,
+                             const float4* __restrict__ partial, int ldy4, int nvec,
+                             float4* __restrict__ Y) {
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n_split) return;
+  int seg = split_seg[w], f = split_first[w], c = split_count[w];
+#pragma unroll
+  for (int q = 0; q < VPL; ++q) {
+    int vi = lane + 32 * q;
+    if (vi >= nvec) continue;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < c; ++t) {
+      float4 p = partial[(int64_t)(f + t) * ldy4 + vi];
+      a.x += p.x; a.y += p.y; a.z += p.z; a.w += p.w;
+    }
+    Y[(int64_t)seg * ldy4 + vi] = a;
+  }
+}
+
+// ------------------------------------------------------------------- SpMV
+__global__ void __launch_bounds__(256)
+    k_spmv(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
+           const int2* __restrict__ items, const int* __restrict__ item_slot, int n_items,
+           const float* __restrict__ x, float* __restrict__ y, float* __restrict__ partial) {
+  int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (item >= n_items) return;
+  int2 it = items[item];
+  int seg = it.x, beg = it.y;
+  int end = min(beg + kSplit, ptr[seg + 1]);
+  float a = 0.f;
+  for (int p = beg + lane; p < end; p += 32) a = fmaf(val[p], __ldg(&x[idx[p]]), a);
+  a = warp_sum(a);
+  if (lane == 0) {
+    int slot = item_slot[item];
+    if (slot < 0)
+      y[seg] = a;
+    else
+      partial[slot] = a;
+  }
+}
+
+__global__ void k_spmv_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
+                             const int* __restrict__ split_count, int n_split,
+                             const float* __restrict__ partial, float* __restrict__ y) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_split) return;
+  float a = 0.f;
+  for (int t = 0; t < split_count[w]; ++t) a += partial[split_first[w] + t];
+  y[split_seg[w]] = a;
+}
+
+}  // namespace
+
+// ======================================================================= API
+void launch_row_ids(const int* ptr, int nseg, int* rows, cudaStream_t s) {
+  if (nseg <= 0) return;
+  int warps_per_block = 8;
+  k_row_ids<<<(nseg + warps_per_block - 1) / warps_per_block, 256, 0, s>>>(ptr, nseg, rows);
+  SFD_LAUNCH_CHECK();
+}
+
+void launch_check_entries(const int* idx, const float* val, int64_t nnz, int d, int* col_count,
+                          double* fro2_out, int* flags, cudaStream_t s) {
+  // fro2_out[0] receives the total; fro2_out[1..kCheckBlocks] hold block partials
+  int nb = (int)std::min<int64_t>(kCheckBlocks, std::max<int64_t>(1, (nnz + 1023) / 1024));
+  k_check_entries<<<nb, 256, 0, s>>>(idx, val, nnz, d, col_count, fro2_out + 1, flags);
+  SFD_LAUNCH_CHECK();
+  k_sum_doubles<<<1, 256, 0, s>>>(fro2_out + 1, nb, fro2_out);
+  SFD_LAUNCH_CHECK();
+}
+
+void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_t s) {
+  int nb = std::max(1, (n + kScanChunk - 1) / kScanChunk);
+  k_scan_block_sums<<<nb, 1024, 0, s>>>(in, n, tmp);
+  SFD_LAUNCH_CHECK();
+  k_scan_top<<<1, 1024, 0, s>>>(tmp, nb);
+  SFD_LAUNCH_CHECK();
+  k_scan_final<<<nb, 1024, 0, s>>>(in, n, tmp, out);
+  SFD_LAUNCH_CHECK();
+}
+
+void radix_sort_by_key(int* key, int* a, float* b, int* key_alt, int* a_alt, float* b_alt,
+                       int64_t n, int bits, int* hist, int* scan_tmp, cudaStream_t s) {
+  // Even number of 8-bit passes so the result lands back in (key, a, b).
+  int passes = std::max(2, (bits + 7) / 8);
+  if (passes & 1) ++passes;
+  if (n <= 0) return;
+  int ntiles = (int)((n + kRadixTile - 1) / kRadixTile);
+  int* k0 = key; int* a0 = a; float* b0 = b;
+  int* k1 = key_alt; int* a1 = a_alt; float* b1 = b_alt;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    if (shift >= 31) shift = 31;  // padding passes past the key width are no-ops (digit 0)
+    k_radix_hist<<<ntiles, kRadixWarps * 32, 0, s>>>(k0, n, shift, ntiles, hist);
+    SFD_LAUNCH_CHECK();
+    exclusive_scan(hist, 256 * ntiles, hist + 256 * ntiles + 1, scan_tmp, s);
+    k_radix_scatter<<<ntiles, kRadixWarps * 32, 0, s>>>(k0, a0, b0, n, shift, ntiles,
+                                                       hist + 256 * ntiles + 1, k1, a1, b1);
+    SFD_LAUNCH_CHECK();
+    std::swap(k0, k1); std::swap(a0, a1); std::swap(b0, b1);
+  }
+}
+
+void build_work(Csr& c, cudaStream_t s) {
+  SegWork& w = c.work;
+  int n = c.nseg;
+  if (n <= 0) {
+    w.n_items = w.n_split = w.n_slots = 0;
+    return;
+  }
+  // counts in split_seg/split_first/split_count scratch, offsets into item_slot area
+  int* cnt_items = w.split_seg;     // reused as scratch before fill
+  int* cnt_slots = w.split_first;
+  int* cnt_split = w.split_count;
+  k_count_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, cnt_items, cnt_slots, cnt_split);
+  SFD_LAUNCH_CHECK();
+  int* off = w.counters + 8;  // 3 * (n + 1) ints of offsets
+  int* item_off = off;
+  int* slot_off = off + (n + 1);
+  int* split_off = off + 2 * (n + 1);
+  int* tmp = off + 3 * (n + 1);
+  exclusive_scan(cnt_items, n, item_off, tmp, s);
+  exclusive_scan(cnt_slots, n, slot_off, tmp, s);
+  exclusive_scan(cnt_split, n, split_off, tmp, s);
+  int h[3];
+  SFD_CUDA(cudaMemcpyAsync(&h[0], item_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFD_CUDA(cudaMemcpyAsync(&h[1], split_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFD_CUDA(cudaMemcpyAsync(&h[2], slot_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFD_CUDA(cudaStreamSynchronize(s));
+  w.n_items = h[0];
+  w.n_split = h[1];
+  w.n_slots = h[2];
+  if (w.n_items > w.cap_items) throw CudaError{cudaErrorMemoryAllocation, "work list capacity"};
+  // the counts scratch aliases split_*: copy offsets first is not needed, fill reads offsets only
+  k_fill_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, item_off, slot_off, split_off, w.items,
+                                               w.item_slot, w.split_seg, w.split_first,
+                                               w.split_count);
+  SFD_LAUNCH_CHECK();
+}
+
+void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
+          cudaStream_t s) {
+  const SegWork& w = c.work;
+  int nvec = (k + 3) / 4;
+  int grid = (w.n_items + 7) / 8;
+  if (w.n_items > 0) {
+    if (nvec <= 32)
+      k_spmm<1><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
+                                     (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                     (float4*)partial);
+    else
+      k_spmm<2><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
+                                     (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                     (float4*)partial);
+    SFD_LAUNCH_CHECK();
+  }
+  if (w.n_split > 0) {
+    int g2 = (w.n_split + 7) / 8;
+    if (nvec <= 32)
+      k_spmm_fixup<1><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.n_split,
+                                         (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+    else
+      k_spmm_fixup<2><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.n_split,
+                                         (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+    SFD_LAUNCH_CHECK();
+  }
+}
+
+void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s) {
+  const SegWork& w = c.work;
+  if (w.n_items > 0) {
+    k_spmv<<<(w.n_items + 7) / 8, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
+                                               w.n_items, x, y, partial);
+    SFD_LAUNCH_CHECK();
+  }
+  if (w.n_split > 0) {
+    k_spmv_fixup<<<(w.n_split + 127) / 128, 128, 0, s>>>(w.split_seg, w.split_first,
+                                                         w.split_count, w.n_split, partial, y);
+    SFD_LAUNCH_CHECK();
+  }
+}
+
+}  // namespace sfd

@@ -1,0 +1,162 @@
+// VerifySpectral (Alg. 6, Sec. 4.1) on C = (A'^T A' - B'^T B') / (Delta / 2)
+// as BoostedSparseShrink (Alg. 4) calls it. x is a Philox Gaussian vector
+// normalised to the unit sphere; p power steps keep x normalised and add
+// log ||C x_t|| to a running sum, so ||C^p x|| never overflows. Accept iff the
+// sum is <= 0 (the host compares).
+//
+// One step: u = A' x (CSR), w = B' x (reduction over the d rows of B'^T),
+// v = A'^T u (CSC) - B'^T w, ||v||, x <- v / ||v||. Every reduction runs in a
+// fixed order (deterministic).
+#include <math.h>
+
+#include <algorithm>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+
+namespace {
+
+constexpr int kVsBlocks = 256;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[b] = sum over rows of block b's stripe of x_j^2 (fp32 in-block, fixed grid)
+__global__ void k_norm2_partial(const float* __restrict__ x, int64_t n, float* __restrict__ part) {
+  float a = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a = fmaf(x[i], x[i], a);
+  __shared__ float red[32];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+// scal[0] logsum, scal[1] inverse norm of the current x, scal[2] 1 if some C x_t was 0.
+// mode 0: initial normalisation (no log term); mode 1: a power step with factor `scale`.
+__global__ void k_norm_finalize(const float* __restrict__ part, int nb, double scale, int mode,
+                                double* __restrict__ scal) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) a += (double)part[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double n2 = sh[0];
+    if (mode == 0) scal[0] = 0.0;
+    if (n2 > 0.0) {
+      if (mode == 1) scal[0] += log(scale) + 0.5 * log(n2);
+      scal[1] = 1.0 / sqrt(n2);
+    } else {
+      scal[1] = 0.0;
+      if (mode == 1) scal[2] = 1.0;
+    }
+  }
+}
+
+__global__ void k_scale(float* __restrict__ x, int64_t n, const double* __restrict__ scal) {
+  const float s = (float)scal[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+// wpart[b][c] = sum over the rows j of stripe b of Bt[j][c] * x[j]
+__global__ void k_btx_partial(const float* __restrict__ Bt, int ld, int ell, int64_t d,
+                              const float* __restrict__ x, float* __restrict__ wpart) {
+  const int c = threadIdx.x;
+  const int64_t rows = (d + gridDim.x - 1) / gridDim.x;
+  const int64_t j0 = blockIdx.x * rows, j1 = min(d, j0 + rows);
+  float a = 0.f;
+  if (c < ell)
+    for (int64_t j = j0; j < j1; ++j) a = fmaf(Bt[j * ld + c], x[j], a);
+  if (c < ell) wpart[blockIdx.x * ell + c] = a;
+}
+
+__global__ void k_btx_reduce(const float* __restrict__ wpart, int nb, int ell,
+                             float* __restrict__ w) {
+  int c = threadIdx.x;
+  if (c >= ell) return;
+  float a = 0.f;
+  for (int b = 0; b < nb; ++b) a += wpart[b * ell + c];
+  w[c] = a;
+}
+
+// v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block (fixed grid)
+__global__ void __launch_bounds__(256)
+    k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
+               const float* __restrict__ w, float* __restrict__ part) {
+  __shared__ float ws[kMaxEll];
+  __shared__ float red[8];
+  for (int c = threadIdx.x; c < ell; c += blockDim.x) ws[c] = w[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  float acc2 = 0.f;
+  for (int64_t j = (int64_t)blockIdx.x * 8 + wp; j < d; j += (int64_t)gridDim.x * 8) {
+    float s = 0.f;
+    for (int c = lane; c < ell; c += 32) s = fmaf(Bt[j * ld + c], ws[c], s);
+    s = warp_sum(s);
+    float nv = v[j] - s;
+    if (lane == 0) {
+      v[j] = nv;
+      acc2 = fmaf(nv, nv, acc2);
+    }
+  }
+  if (lane == 0) red[wp] = acc2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+}  // namespace
+
+double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
+  float* x = ws.vec0;   // d
+  float* u = ws.vec1;   // m
+  float* v = ws.vec2;   // d
+  float* w = ws.wpart + kVsBlocks * kMaxEll;  // ell
+  float* part = ws.wpart + kVsBlocks * kMaxEll + kMaxEll;  // kVsBlocks
+  double* scal = ws.scalars + 8;
+  SFD_CUDA(cudaMemsetAsync(scal, 0, 4 * sizeof(double), s));
+  launch_gauss_fill(x, a.d, 1, 1, a.seed, a.b, a.r, 2 /* tag of Alg. 6's x */, s);
+  k_norm2_partial<<<kVsBlocks, 256, 0, s>>>(x, a.d, part);
+  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, 1.0, 0, scal);
+  k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
+  SFD_LAUNCH_CHECK();
+  for (int t = 0; t < a.p; ++t) {
+    spmv(*a.csr, x, u, ws.partial_rows, s);
+    k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, ws.wpart);
+    k_btx_reduce<<<1, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
+    spmv(*a.csc, u, v, ws.partial_rows, s);
+    k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
+    k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale, 1, scal);
+    SFD_LAUNCH_CHECK();
+    std::swap(x, v);
+    k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
+    SFD_LAUNCH_CHECK();
+  }
+  double h[3];
+  SFD_CUDA(cudaMemcpyAsync(h, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SFD_CUDA(cudaStreamSynchronize(s));
+  if (h[2] != 0.0) return -INFINITY;
+  return h[0];
+}
+
+}  // namespace sfd

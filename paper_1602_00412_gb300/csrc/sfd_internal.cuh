@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libsfd.so.
+// Nothing here is part of the C ABI (include/sfd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sfd.h"
+
+namespace sfd {
+
+// Dense blocks are row-major with the leading dimension padded to a multiple
+// of 8 floats, so every row starts on a 32-byte sector and float4 accesses
+// are aligned. Padding columns are kept at zero.
+inline int ld_of(int k) { return (k + 7) & ~7; }
+
+constexpr int kMaxEll = 256;      // largest sketch size l
+constexpr int kMaxEig = 512;      // largest symmetric eigenproblem (2 l)
+constexpr int kSplit = 2048;      // entries per work item of the sparse products
+constexpr float kAlpha = 6.0f / 41.0f;  // alpha of Alg. 4
+
+struct CudaError {
+  cudaError_t err;
+  const char* where;
+};
+
+// Throwing check used inside the library; the C ABI layer catches it.
+#define SFD_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) throw ::sfd::CudaError{e__, #call}; \
+  } while (0)
+
+// Every kernel launch is followed by this check; it also counts launches
+// (process-wide) so callers can report how many kernels ran.
+extern unsigned long long g_kernel_launches;
+#define SFD_LAUNCH_CHECK()                 \
+  do {                                     \
+    __atomic_add_fetch(&::sfd::g_kernel_launches, 1ull, __ATOMIC_RELAXED); \
+    SFD_CUDA(cudaGetLastError());          \
+  } while (0)
+
+// A CSR-like structure on the device (rows of A' for the CSR copy, columns
+// for the CSC copy) plus the work list that splits long segments.
+struct SegWork {
+  int2* items = nullptr;     // (segment, begin) ; end = min(begin + kSplit, ptr[seg+1])
+  int* item_slot = nullptr;  // -1: item covers its whole segment, else partial slot
+  int* split_seg = nullptr;  // segments cut into several items
+  int* split_first = nullptr;// first item of each split segment
+  int* split_count = nullptr;// items of each split segment
+  int* counters = nullptr;   // [0] items, [1] split segments, [2] slots
+  int n_items = 0, n_split = 0, n_slots = 0;  // host copies
+  int cap_items = 0;
+};
+
+struct Csr {
+  int* ptr = nullptr;   // nseg + 1
+  int* idx = nullptr;   // nnz
+  float* val = nullptr; // nnz
+  int nseg = 0;
+  int64_t nnz = 0;
+  SegWork work;
+};
+
+// Scratch owned by a context (or by a one-shot call).
+struct Workspace {
+  // small dense
+  float* gram_partial = nullptr;  // [chunks][tiles] 64x64 partial tiles
+  int gram_partial_cap = 0;       // floats
+  float* small_a = nullptr;       // kMaxEig^2 floats: Gram / eigen input
+  float* small_b = nullptr;       // kMaxEig^2 floats: R^-1 / eigenvectors / weights
+  float* evals = nullptr;         // kMaxEig
+  float* eig_work = nullptr;      // eigensolver scratch
+  double* scalars = nullptr;      // device scalars (norms, logs)
+  int* flags = nullptr;           // device status words
+  // sparse helpers
+  int* tmp_i0 = nullptr;
+  int* tmp_i1 = nullptr;
+  float* tmp_f0 = nullptr;
+  int* hist = nullptr;
+  int hist_cap = 0;
+  int* scan_tmp = nullptr;
+  float* partial_rows = nullptr;  // split-segment partial outputs [slots][ld]
+  int partial_rows_cap = 0;       // rows
+  float* vec0 = nullptr;          // VS vectors
+  float* vec1 = nullptr;
+  float* vec2 = nullptr;
+  float* wpart = nullptr;         // VS B'x partials
+};
+
+// ---------------------------------------------------------------- sparse ops
+// Row ids of each entry of a CSR (expand ptr).
+void launch_row_ids(const int* ptr, int nseg, int* rows, cudaStream_t s);
+// Validate a buffer slice: indices in [0,d), finite values; column counts
+// (atomic), sum of squares partials. Sets flags[0] on a bad index/value.
+void launch_check_entries(const int* idx, const float* val, int64_t nnz, int d, int* col_count,
+                          double* fro2_out, int* flags, cudaStream_t s);
+// Exclusive scan of n ints (n >= 0) into out[0..n]; out[n] = total.
+void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_t s);
+// Stable LSD radix sort of (key, a, b) by key in [0, 2^bits): CSR -> CSC.
+void radix_sort_by_key(int* key, int* a, float* b, int* key_alt, int* a_alt, float* b_alt,
+                       int64_t n, int bits, int* hist, int* scan_tmp, cudaStream_t s);
+// Work list of a segmented structure (split segments longer than kSplit).
+void build_work(Csr& c, cudaStream_t s);
+// Y[seg, 0:k] = sum over entries of seg: val * X[idx, 0:k]  (k <= 256, lds % 4 == 0)
+void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
+          cudaStream_t s);
+// y[seg] = scale_ptr? * sum val * x[idx]
+void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s);
+
+// ----------------------------------------------------------------- dense ops
+// Philox4x64-10 Gaussian fill: out[i*ld + j] = normal #(i*cols + j) of (seed,b,r,tag).
+void launch_gauss_fill(float* out, int64_t rows, int cols, int ld, uint64_t seed, uint64_t b,
+                       uint64_t r, uint64_t tag, cudaStream_t s);
+// Column map of a dense operand: columns [0,k0) at offset 0, [k0, k0+k1) at offset off1.
+struct ColMap {
+  int k0, k1, off1;
+  __host__ __device__ int total() const { return k0 + k1; }
+  __host__ __device__ int col(int c) const { return c < k0 ? c : off1 + (c - k0); }
+};
+// G = X^T X (n x n, n = map.total(), row-major ld n) over `rows` rows.
+void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
+          cudaStream_t s);
+// Y[:, 0:kout] = X[:, map] * T (T: n x kout row-major, ld kout).
+void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout, float* Y,
+             int ldy, cudaStream_t s);
+// Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
+// row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
+// clamped.
+void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s);
+// Largest nwant eigenpairs of the symmetric n x n S: evals (descending),
+// evecs n x nwant row-major.
+void symeig(const float* S, int n, int nwant, float* evals, float* evecs, float* work,
+            cudaStream_t s);
+size_t symeig_work_floats(int n, int nwant);
+// Shrink weights with threshold thr = ev[nkeep-1] (thr_zero: thr = 0, the
+// case of fewer than l rows): T[i][j] = evecs[i][j] * sqrt(max(0, 1 - thr/ev[j]))
+// for j < nkeep (0 where ev[j] <= thr or ev[j] <= 0); scal[0] =
+// sum_j max(0, ev[j] - thr), the squared Frobenius norm of the shrunk sketch.
+void shrink_weights(const float* evals, const float* evecs, int n, int nwant, int nkeep,
+                    int thr_zero, float* T, double* scal, cudaStream_t s);
+// out (cols x rows, row-major, ld_out) = in^T  (in: rows x cols, ld_in)
+void transpose(const float* in, int64_t rows, int cols, int ld_in, float* out, int64_t ld_out,
+               cudaStream_t s);
+// Scatter a CSR block (rows x d) densely and transposed into out (d x ld, zeroed first).
+void csr_to_dense_t(const int* ptr, const int* idx, const float* val, int rows, int64_t d,
+                    float* out, int ld, cudaStream_t s);
+
+// ------------------------------------------------------------ VerifySpectral
+struct VsArgs {
+  const Csr* csr;
+  const Csr* csc;
+  const float* Bt;  // d x ld (B'^T)
+  int ld, ell;
+  int64_t d, m;
+  double scale;     // 2 / Delta
+  int p;
+  uint64_t seed, b, r;
+};
+// Runs p power steps; returns log ||C^p x|| (host value).
+double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s);
+
+}  // namespace sfd

@@ -1,0 +1,252 @@
+"""ctypes binding of libsfd.so (include/sfd.h): the same entry points, with
+argument marshalling only. Host arrays are numpy arrays; device arrays are
+torch CUDA tensors (PyTorch supplies device memory and streams). Every
+computation runs in the library's CUDA kernels; if the library is missing,
+loading fails loudly.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsfd.so")
+
+SFD_ABI_VERSION = 1
+SFD_OK, SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA, SFD_EVERIFY, SFD_ETIMEOUT = 0, 1, 2, 3, 4, 5
+SFD_HOST, SFD_DEVICE = 0, 1
+
+
+class SfdError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__("sfd error %d (%s)%s" % (code, _strerror(code), (": " + msg) if msg else ""))
+
+
+class sfd_options(ctypes.Structure):
+    _fields_ = [("abi_version", ctypes.c_uint32), ("delta", ctypes.c_double),
+                ("verify", ctypes.c_int32), ("c_q", ctypes.c_double),
+                ("q_override", ctypes.c_int32), ("retry_cap", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("q_mode", ctypes.c_int32),
+                ("strict", ctypes.c_int32), ("inject_vs_fail", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
+
+
+class sfd_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("rows_seen", "nnz_seen", "buffers", "attempts",
+                                               "vs_rejects", "unverified", "q_total",
+                                               "pending_rows", "pending_nnz")] + \
+               [(n, ctypes.c_double) for n in ("last_delta", "last_logsum", "last_fro2")] + \
+               [("kernel_launches", ctypes.c_int64), ("spmm_launches", ctypes.c_int64),
+                ("spmm_ms", ctypes.c_double), ("spmm_bytes", ctypes.c_double)]
+
+
+class sfd_shrink_info(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("attempts", ctypes.c_int32), ("verified", ctypes.c_int32),
+                ("vs_steps", ctypes.c_int32), ("delta_shrink", ctypes.c_double),
+                ("logsum", ctypes.c_double), ("fro2_a", ctypes.c_double),
+                ("fro2_b", ctypes.c_double)]
+
+
+EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "sfd_merge",
+           "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
+           "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig"]
+
+_lib = None
+
+
+def load(path=None):
+    """Load libsfd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libsfd.so not found at %s: build it with "
+                           "paper_1602_00412_gb300.build.build()" % p)
+    L = ctypes.CDLL(p)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    L.sfd_options_init.argtypes = [ctypes.POINTER(sfd_options)]
+    L.sfd_options_init.restype = None
+    L.sfd_create.argtypes = [i64, i32, u64, ctypes.POINTER(sfd_options), ctypes.POINTER(vp)]
+    L.sfd_append_rows.argtypes = [vp, i64, vp, vp, vp, ctypes.c_int]
+    L.sfd_sketch.argtypes = [vp, vp, ctypes.c_int]
+    L.sfd_merge.argtypes = [vp, vp]
+    L.sfd_get_stats.argtypes = [vp, ctypes.POINTER(sfd_stats)]
+    L.sfd_reset.argtypes = [vp]
+    L.sfd_destroy.argtypes = [vp]
+    L.sfd_destroy.restype = None
+    L.sfd_strerror.argtypes = [ctypes.c_int]
+    L.sfd_strerror.restype = ctypes.c_char_p
+    L.sfd_last_error.argtypes = [vp]
+    L.sfd_last_error.restype = ctypes.c_char_p
+    L.sfd_bssh_buffer.argtypes = [i64, i64, i32, vp, vp, vp, u64, i64, ctypes.POINTER(sfd_options),
+                                  vp, ctypes.POINTER(sfd_shrink_info)]
+    L.sfd_dense_shrink.argtypes = [i64, i64, i32, vp, vp]
+    L.sfd_csr_spmm.argtypes = [i64, i64, vp, vp, vp, i32, vp, i32, vp, i32, i32]
+    L.sfd_orthonormalize.argtypes = [i64, i32, vp, i32]
+    L.sfd_symeig.argtypes = [i32, vp, i32, vp, vp]
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error"):
+            fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _strerror(code):
+    try:
+        return load().sfd_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _check(rc, ctx=None):
+    if rc != SFD_OK:
+        msg = ""
+        if ctx is not None:
+            msg = (load().sfd_last_error(ctx) or b"").decode()
+        raise SfdError(rc, msg)
+
+
+def _is_torch_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x, dtype):
+    """(pointer, where) for a numpy array or a torch CUDA tensor of `dtype`."""
+    if x is None:
+        return None, SFD_HOST
+    if _is_torch_cuda(x):
+        import torch
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError("device array must be a contiguous %s tensor" % tdt)
+        return ctypes.c_void_p(x.data_ptr()), SFD_DEVICE
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("host array must be a C-contiguous %s array" % np.dtype(dtype))
+    return ctypes.c_void_p(a.ctypes.data), SFD_HOST
+
+
+def options(**kw):
+    o = sfd_options()
+    load().sfd_options_init(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+# --------------------------------------------------------------- entry points
+def sfd_create(d, ell, seed, opts=None):
+    h = ctypes.c_void_p()
+    _check(load().sfd_create(d, ell, seed, ctypes.byref(opts) if opts is not None else None,
+                             ctypes.byref(h)))
+    return h
+
+
+def sfd_append_rows(ctx, indptr, indices, values):
+    """indptr (n+1 int64), indices (int32), values (float32): all numpy, or all
+    torch CUDA tensors."""
+    n = len(indptr) - 1
+    pi, w1 = _ptr(indptr, np.int64)
+    px, w2 = _ptr(indices, np.int32)
+    pv, w3 = _ptr(values, np.float32)
+    if not (w1 == w2 == w3):
+        raise TypeError("indptr, indices and values must all be host or all device arrays")
+    _check(load().sfd_append_rows(ctx, n, pi, px, pv, w1), ctx)
+
+
+def sfd_sketch(ctx, out):
+    """Write B (l x d float32) into `out` (numpy array or torch CUDA tensor)."""
+    p, w = _ptr(out, np.float32)
+    _check(load().sfd_sketch(ctx, p, w), ctx)
+    return out
+
+
+def sfd_merge(dst, src):
+    _check(load().sfd_merge(dst, src), dst)
+
+
+def sfd_get_stats(ctx):
+    s = sfd_stats()
+    _check(load().sfd_get_stats(ctx, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in sfd_stats._fields_}
+
+
+def sfd_reset(ctx):
+    _check(load().sfd_reset(ctx), ctx)
+
+
+def sfd_destroy(ctx):
+    load().sfd_destroy(ctx)
+
+
+def sfd_bssh_buffer(m, d, ell, rowptr, colidx, vals, seed, b, Bp_out, opts=None):
+    info = sfd_shrink_info()
+    _check(load().sfd_bssh_buffer(m, d, ell, ctypes.c_void_p(rowptr.data_ptr()),
+                                  ctypes.c_void_p(colidx.data_ptr()),
+                                  ctypes.c_void_p(vals.data_ptr()), seed, b,
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.c_void_p(Bp_out.data_ptr()), ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in sfd_shrink_info._fields_}
+
+
+def sfd_dense_shrink(rows, d, ell, M, B_out):
+    _check(load().sfd_dense_shrink(rows, d, ell, ctypes.c_void_p(M.data_ptr()),
+                                   ctypes.c_void_p(B_out.data_ptr())))
+
+
+def sfd_csr_spmm(m, d, rowptr, colidx, vals, k, X, ldx, Y, ldy, transpose):
+    _check(load().sfd_csr_spmm(m, d, ctypes.c_void_p(rowptr.data_ptr()),
+                               ctypes.c_void_p(colidx.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                               k, ctypes.c_void_p(X.data_ptr()), ldx, ctypes.c_void_p(Y.data_ptr()),
+                               ldy, int(transpose)))
+
+
+def sfd_orthonormalize(rows, k, X, ld):
+    _check(load().sfd_orthonormalize(rows, k, ctypes.c_void_p(X.data_ptr()), ld))
+
+
+def sfd_symeig(n, S, nwant, evals, evecs):
+    _check(load().sfd_symeig(n, ctypes.c_void_p(S.data_ptr()), nwant,
+                             ctypes.c_void_p(evals.data_ptr()), ctypes.c_void_p(evecs.data_ptr())))
+
+
+class SFD:
+    """Stream object over one context: append rows, read the sketch, merge."""
+
+    def __init__(self, d, ell, seed=0, **opts):
+        self.d, self.ell = int(d), int(ell)
+        self._opts = options(**opts) if opts else None
+        self.ctx = sfd_create(self.d, self.ell, seed, self._opts)
+
+    def append(self, indptr, indices, values):
+        sfd_append_rows(self.ctx, indptr, indices, values)
+
+    def sketch(self, out=None):
+        if out is None:
+            out = np.empty((self.ell, self.d), dtype=np.float32)
+        return sfd_sketch(self.ctx, out)
+
+    def merge(self, other):
+        sfd_merge(self.ctx, other.ctx)
+
+    def stats(self):
+        return sfd_get_stats(self.ctx)
+
+    def reset(self):
+        sfd_reset(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            sfd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,173 @@
+"""GPU parity of BoostedSparseShrink (Alg. 4) per buffer and of the whole
+stream (Alg. 2) through the C ABI, against the FP64 oracle on the same seeded
+inputs and Philox keys: B^T B relative Frobenius error <= 1e-4 on the
+gapped-spectrum workload, cov-err within 2% of the oracle's and under the FD
+bound, plus the paths of the API (device input, chunking, flush, merge, retry,
+invalid input)."""
+import numpy as np
+import pytest
+
+from oracle import metrics
+from oracle import sfd as O
+from paper_1602_00412_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_BBT = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1602_00412_gb300 import sfd
+    return sfd
+
+
+def dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+@pytest.mark.parametrize("kind", ["gapped", "c1"])
+def test_bssh_buffer_parity(lib, kind):
+    d, ell, seed, b = 2000, 50, 3, 2
+    X = (synth.c1_gapped if kind == "gapped" else synth.c1)(seed=seed, n=2000)
+    Bp = torch.zeros((ell, d), device="cuda")
+    info = lib.sfd_bssh_buffer(X.n, d, ell, dev(X.indptr, np.int32), dev(X.indices, np.int32),
+                               dev(X.values, np.float32), seed, b, Bp)
+    A = X.to_scipy()
+    q = O.q_fixed(X.n)
+    ref, rinfo = O.boosted_sparse_shrink(A, ell, 0.01, seed, b, q)
+    got = Bp.cpu().numpy().astype(np.float64)
+    rel = metrics.bbt_rel_diff(got, ref)
+    assert info["q"] == q
+    assert info["verified"] == 1 and rinfo["verified"]
+    assert info["attempts"] == rinfo["attempts"]
+    assert abs(info["delta_shrink"] - rinfo["Delta"]) <= 1e-4 * abs(rinfo["Delta"])
+    if kind == "gapped":
+        assert rel <= TOL_BBT, rel
+    else:
+        assert rel <= 1e-2, rel   # no gap at l: the subspace itself is less determined
+    assert np.allclose(got[-1], 0)
+
+
+def _run_gpu(lib, X, d, ell, seed, chunks=None, device=False, **opts):
+    s = lib.SFD(d, ell, seed, **opts)
+    if chunks is None:
+        chunks = [(0, X.n)]
+    for a, b in chunks:
+        part = X.rows(a, b)
+        if device:
+            s.append(dev(part.indptr, np.int64), dev(part.indices, np.int32),
+                     dev(part.values, np.float32))
+        else:
+            s.append(part.indptr, part.indices, part.values)
+    B = s.sketch().astype(np.float64)
+    st = s.stats()
+    s.close()
+    return B, st
+
+
+@pytest.mark.parametrize("kind", ["gapped", "c1"])
+def test_stream_parity_c1(lib, kind):
+    d, ell, k, seed = 2000, 50, 10, 0
+    X = (synth.c1_gapped if kind == "gapped" else synth.c1)(seed=seed)
+    B, st = _run_gpu(lib, X, d, ell, seed)
+    ref, o = O.sfd_stream(X.indptr, X.indices, X.values, d, ell, seed)
+    assert st["buffers"] == len(o.log) == 5
+    A = X.to_scipy()
+    rel = metrics.bbt_rel_diff(B, ref)
+    ce_gpu, ce_ref = metrics.cov_err(A, B), metrics.cov_err(A, ref)
+    print("%s: bbt rel %.2e  cov-err gpu %.4e oracle %.4e" % (kind, rel, ce_gpu, ce_ref))
+    if kind == "gapped":
+        assert rel <= TOL_BBT
+    assert abs(ce_gpu - ce_ref) <= 0.02 * ce_ref
+    assert metrics.cov_norm(A, B) <= metrics.fd_bound(A, ell, k)
+    lo, _ = metrics.residual_eigs(A, B)
+    assert lo >= -1e-5 * metrics.fro2(A)
+
+
+def test_chunking_and_device_input_identical(lib):
+    d, ell, seed = 2000, 50, 1
+    X = synth.c1_gapped(seed=seed, n=5000)
+    B1, _ = _run_gpu(lib, X, d, ell, seed)
+    rng = np.random.default_rng(0)
+    cuts = sorted(set(rng.choice(np.arange(1, X.n), 30, replace=False).tolist()))
+    chunks = list(zip([0] + cuts, cuts + [X.n]))
+    B2, _ = _run_gpu(lib, X, d, ell, seed, chunks=chunks)
+    B3, _ = _run_gpu(lib, X, d, ell, seed, device=True)
+    assert np.array_equal(B1, B2)
+    assert np.array_equal(B1, B3)
+
+
+def test_short_stream_and_flush(lib):
+    d, ell = 300, 20
+    X = synth.planted(13, d, 10, 1.1, 3, 10.0, 0.7, 0.1, 4)   # fewer rows than l
+    B, st = _run_gpu(lib, X, d, ell, 0)
+    A = X.to_scipy().toarray()
+    assert np.abs(B.T @ B - A.T @ A).max() <= 1e-5 * np.abs(A.T @ A).max()
+    X2 = synth.planted(700, d, 10, 1.1, 3, 10.0, 0.7, 0.1, 5)  # 2 full buffers + 100 flushed
+    B2, st2 = _run_gpu(lib, X2, d, ell, 7)
+    ref, o = O.sfd_stream(X2.indptr, X2.indices, X2.values, d, ell, 7)
+    assert st2["buffers"] == len(o.log) == 3
+    assert metrics.bbt_rel_diff(B2, ref) <= 1e-3
+
+
+def test_merge_matches_oracle(lib):
+    d, ell = 2000, 50
+    X = synth.c1_gapped(seed=2, n=6000)
+    a = lib.SFD(d, ell, 11)
+    b = lib.SFD(d, ell, 12)
+    pa, pb = X.rows(0, 3500), X.rows(3500, 6000)
+    a.append(pa.indptr, pa.indices, pa.values)
+    b.append(pb.indptr, pb.indices, pb.values)
+    a.merge(b)
+    B = a.sketch().astype(np.float64)
+    oa, ob = O.SFDOracle(d, ell, 11), O.SFDOracle(d, ell, 12)
+    oa.append_rows(pa.indptr, pa.indices, pa.values)
+    ob.append_rows(pb.indptr, pb.indices, pb.values)
+    oa.merge(ob)
+    assert metrics.bbt_rel_diff(B, oa.sketch()) <= TOL_BBT
+    a.close(); b.close()
+
+
+def test_retry_path_with_injected_failures(lib):
+    d, ell, seed = 2000, 50, 5
+    X = synth.c1_gapped(seed=seed, n=4000)
+    B, st = _run_gpu(lib, X, d, ell, seed, inject_vs_fail=3)
+    ref, o = O.sfd_stream(X.indptr, X.indices, X.values, d, ell, seed, inject_fail=3)
+    assert st["attempts"] == sum(e["attempts"] for e in o.log) == 2 + 3
+    assert st["vs_rejects"] == 3
+    assert metrics.bbt_rel_diff(B, ref) <= TOL_BBT
+    # retry cap reached: kept unverified, strict mode reports it
+    s = lib.SFD(d, ell, seed, inject_vs_fail=20, retry_cap=2, strict=1)
+    part = X.rows(0, 2000)
+    with pytest.raises(lib.SfdError) as ei:
+        s.append(part.indptr, part.indices, part.values)
+    assert ei.value.code == lib.SFD_EVERIFY
+    assert s.stats()["unverified"] == 1
+    s.close()
+
+
+def test_invalid_input_leaves_context_usable(lib):
+    d, ell, seed = 500, 20, 0
+    X = synth.planted(1200, d, 10, 1.1, 3, 10.0, 0.7, 0.1, 9)
+    good, _ = _run_gpu(lib, X, d, ell, seed)
+    s = lib.SFD(d, ell, seed)
+    a = X.rows(0, 300)
+    s.append(a.indptr, a.indices, a.values)
+    bad_idx = a.indices.copy(); bad_idx[5] = d
+    bad_val = a.values.copy(); bad_val[3] = np.nan
+    bad_ptr = a.indptr.copy(); bad_ptr[4] = bad_ptr[5] + 1
+    for ip, ix, vv in [(a.indptr, bad_idx, a.values), (a.indptr, a.indices, bad_val),
+                       (bad_ptr, a.indices, a.values)]:
+        with pytest.raises(lib.SfdError) as ei:
+            s.append(ip, ix, vv)
+        assert ei.value.code == lib.SFD_EINVAL
+    rest = X.rows(300, X.n)
+    s.append(rest.indptr, rest.indices, rest.values)
+    assert np.array_equal(s.sketch().astype(np.float64), good)
+    s.close()
