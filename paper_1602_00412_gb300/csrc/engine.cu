@@ -168,7 +168,7 @@ struct Engine {
       Y = alloc<float>(dense);
       Y2 = alloc<float>(dense);
       for (float* p : {W, W2, Y, Y2}) SFD_CUDA(cudaMemsetAsync(p, 0, dense * sizeof(float), stream));
-      ws.gram_partial = alloc<float>((size_t)640 * 64 * 64 + 256);
+      ws.gram_partial = alloc<float>((size_t)320 * 128 * 128);
       ws.small_a = alloc<float>((size_t)kMaxEig * kMaxEig);
       ws.small_b = alloc<float>((size_t)kMaxEig * kMaxEig);
       ws.evals = alloc<float>(kMaxEig);
@@ -187,7 +187,7 @@ struct Engine {
       ws.vec0 = alloc<float>(d);
       ws.vec1 = alloc<float>(std::max<int64_t>(d, cap_rows));
       ws.vec2 = alloc<float>(d);
-      ws.wpart = alloc<float>(256 * kMaxEll + kMaxEll + 256);
+      ws.wpart = alloc<float>(512 * kMaxEll + kMaxEll + 512);
       fro2_dev = alloc<double>(1024 + 8);
       SFD_CUDA(cudaStreamSynchronize(stream));
     } catch (...) {
@@ -222,8 +222,7 @@ struct Engine {
   double build_structures(int m, int64_t nnz) {
     csr.nseg = m;
     csr.nnz = nnz;
-    SFD_CUDA(cudaMemsetAsync(col_count, 0, (d + 1) * sizeof(int), stream));
-    launch_check_entries(csr.idx, csr.val, nnz, (int)d, col_count, fro2_dev, ws.flags, stream);
+    launch_check_entries(csr.idx, csr.val, nnz, (int)d, nullptr, fro2_dev, ws.flags, stream);
     build_work(csr, stream);  // syncs the stream (reads work-list sizes)
     // CSC by a stable radix sort of (col, row, val) by col
     int* key = key_alt;
@@ -235,7 +234,7 @@ struct Engine {
     // ping-pong partners: the CSR arrays stay intact, so use dedicated alternates
     radix_sort_by_key(key, rows, vals, key_alt2, a_alt, b_alt, nnz, bits_for(d), ws.hist,
                       ws.scan_tmp, stream);
-    exclusive_scan(col_count, (int)d, csc.ptr, ws.scan_tmp, stream);
+    colptr_from_sorted(key, nnz, (int)d, csc.ptr, stream);  // keys now sorted by column
     csc.nseg = (int)d;
     csc.nnz = nnz;
     build_work(csc, stream);
@@ -544,8 +543,7 @@ int sfd_append_rows(sfd_ctx* ctx, int64_t nrows, const int64_t* indptr, const in
     }
     if (total > 0) {
       SFD_CUDA(cudaMemsetAsync(E.ws.flags, 0, sizeof(int), E.stream));
-      SFD_CUDA(cudaMemsetAsync(E.col_count, 0, (E.d + 1) * sizeof(int), E.stream));
-      launch_check_entries(didx, dval, total, (int)E.d, E.col_count, E.fro2_dev, E.ws.flags, E.stream);
+      launch_check_entries(didx, dval, total, (int)E.d, nullptr, E.fro2_dev, E.ws.flags, E.stream);
       int bad = 0;
       SFD_CUDA(cudaMemcpyAsync(&bad, E.ws.flags, sizeof(int), cudaMemcpyDeviceToHost, E.stream));
       SFD_CUDA(cudaStreamSynchronize(E.stream));

@@ -70,10 +70,23 @@ __global__ void k_gauss_fill(float* __restrict__ out, int64_t rows, int cols, in
 }
 
 // ------------------------------------------------------------------ Gram
-constexpr int kT = 64;   // output tile
-constexpr int kR = 32;   // rows per smem stage
+// 128 x 128 output tiles, 16 x 16 threads with 8 x 8 register micro-tiles:
+// per staged row each thread does 64 FMAs for 4 float4 shared loads.
+constexpr int kT = 128;  // output tile
+constexpr int kR = 16;   // rows (Gram) / inner dimension (GEMM) per stage
+constexpr int kGramBlocks = 304;  // split-K blocks per Gram, ~2 per SM
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void fma8x8(float (&acc)[8][8], const float4& a0, const float4& a1,
+                                       const float4& b0, const float4& b1) {
+  const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+}
+
+__global__ void __launch_bounds__(256, 2)
     k_gram_tiles(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
                  int64_t rows_per_chunk, int ntiles, int npairs, float* __restrict__ partial) {
   __shared__ __align__(16) float As[kR][kT];
@@ -83,39 +96,44 @@ __global__ void __launch_bounds__(256)
   int ti = 0, start = 0;
   while (start + (ntiles - ti) <= tp) { start += ntiles - ti; ++ti; }
   const int tj = ti + (tp - start);
+  const bool diag = ti == tj;
   const int n = map.total();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4] = {};
-  int64_t r_beg = (int64_t)chunk * rows_per_chunk;
-  int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  float acc[8][8] = {};
+  const int64_t r_beg = (int64_t)chunk * rows_per_chunk;
+  const int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  float (*Bp)[kT] = diag ? As : Bs;
   for (int64_t r0 = r_beg; r0 < r_end; r0 += kR) {
 #pragma unroll
     for (int q = 0; q < (kR * kT) / 256; ++q) {
-      int li = threadIdx.x + q * 256;
-      int rr = li / kT, cc = li % kT;
-      int64_t g = r0 + rr;
-      int ca = ti * kT + cc, cb = tj * kT + cc;
+      const int li = threadIdx.x + q * 256;
+      const int rr = li / kT, cc = li % kT;
+      const int64_t g = r0 + rr;
+      const int ca = ti * kT + cc;
       As[rr][cc] = (g < r_end && ca < n) ? X[g * ldx + map.col(ca)] : 0.f;
-      Bs[rr][cc] = (g < r_end && cb < n) ? X[g * ldx + map.col(cb)] : 0.f;
+      if (!diag) {
+        const int cb = tj * kT + cc;
+        Bs[rr][cc] = (g < r_end && cb < n) ? X[g * ldx + map.col(cb)] : 0.f;
+      }
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int rr = 0; rr < kR; ++rr) {
-      float4 a = *reinterpret_cast<const float4*>(&As[rr][ty * 4]);
-      float4 bv = *reinterpret_cast<const float4*>(&Bs[rr][tx * 4]);
-      float av[4] = {a.x, a.y, a.z, a.w}, bw[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[rr][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[rr][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bp[rr][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bp[rr][tx * 8 + 4]);
+      fma8x8(acc, a0, a1, b0, b1);
     }
     __syncthreads();
   }
   float* out = partial + ((int64_t)chunk * npairs + tp) * (kT * kT);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    *reinterpret_cast<float4*>(&out[(ty * 4 + i) * kT + tx * 4]) =
-        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  for (int i = 0; i < 8; ++i) {
+    float4* o = reinterpret_cast<float4*>(&out[(ty * 8 + i) * kT + tx * 8]);
+    o[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    o[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
 }
 
 __global__ void k_gram_reduce(const float* __restrict__ partial, int nchunks, int npairs,
@@ -125,59 +143,68 @@ __global__ void k_gram_reduce(const float* __restrict__ partial, int nchunks, in
   int i = (int)(e / n), j = (int)(e % n);
   int a = i, c = j;
   if (a / kT > c / kT) { int t = a; a = c; c = t; }   // use the upper tile (ti <= tj)
-  int ti = a / kT, tj = c / kT;
-  // pair index of (ti, tj), ti <= tj, row-major over the upper triangle of tiles
-  int tp = ti * ntiles - ti * (ti - 1) / 2 + (tj - ti);
-  int off = (a % kT) * kT + (c % kT);
-  float s = 0.f;
-  for (int ch = 0; ch < nchunks; ++ch) s += partial[((int64_t)ch * npairs + tp) * (kT * kT) + off];
-  G[e] = s;
+  const int ti = a / kT, tj = c / kT;
+  const int tp = ti * ntiles - ti * (ti - 1) / 2 + (tj - ti);
+  const int off = (a % kT) * kT + (c % kT);
+  const float* p = partial + (int64_t)tp * (kT * kT) + off;
+  const int64_t stride = (int64_t)npairs * (kT * kT);
+  // four interleaved accumulators, combined in a fixed order (deterministic)
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int ch = 0;
+  for (; ch + 4 <= nchunks; ch += 4) {
+    s0 += p[(ch + 0) * stride];
+    s1 += p[(ch + 1) * stride];
+    s2 += p[(ch + 2) * stride];
+    s3 += p[(ch + 3) * stride];
+  }
+  for (; ch < nchunks; ++ch) s0 += p[ch * stride];
+  G[e] = (s0 + s1) + (s2 + s3);
 }
 
 // ---------------------------------------------------------------- X * T
-__global__ void __launch_bounds__(256)
+// Y[rows, 0:kout] = X[rows, map] T : 128-row x 128-column output tiles, the
+// inner dimension staged 16 at a time (X tile stored transposed so each
+// thread reads its 8 rows as two float4).
+__global__ void __launch_bounds__(256, 2)
     k_gemm_ts(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
               const float* __restrict__ T, int kout, float* __restrict__ Y, int ldy) {
-  __shared__ float Xs[kT][kR + 1];
+  __shared__ __align__(16) float Xs[kR][kT + 4];
   __shared__ __align__(16) float Ts[kR][kT];
   const int n = map.total();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t row0 = (int64_t)blockIdx.x * kT;
   const int col0 = blockIdx.y * kT;
-  float acc[4][4] = {};
+  float acc[8][8] = {};
   for (int c0 = 0; c0 < n; c0 += kR) {
 #pragma unroll
     for (int q = 0; q < (kT * kR) / 256; ++q) {
-      int li = threadIdx.x + q * 256;
-      int rr = li / kR, cc = li % kR;
-      int64_t g = row0 + rr;
-      int c = c0 + cc;
-      Xs[rr][cc] = (g < rows && c < n) ? X[g * ldx + map.col(c)] : 0.f;
-      int tr = li / kT, tc = li % kT;
-      int cr = c0 + tr, oc = col0 + tc;
+      const int li = threadIdx.x + q * 256;
+      const int rr = li / kR, cc = li % kR;     // X tile: 128 rows x 16 inner
+      const int64_t g = row0 + rr;
+      const int c = c0 + cc;
+      Xs[cc][rr] = (g < rows && c < n) ? X[g * ldx + map.col(c)] : 0.f;
+      const int tr = li / kT, tc = li % kT;     // T tile: 16 inner x 128 out
+      const int cr = c0 + tr, oc = col0 + tc;
       Ts[tr][tc] = (cr < n && oc < kout) ? T[(int64_t)cr * kout + oc] : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int cc = 0; cc < kR; ++cc) {
-      float4 t4 = *reinterpret_cast<const float4*>(&Ts[cc][tx * 4]);
-      float tv[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float xv = Xs[ty * 4 + i][cc];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xv, tv[j], acc[i][j]);
-      }
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[cc][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[cc][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Ts[cc][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Ts[cc][tx * 8 + 4]);
+      fma8x8(acc, a0, a1, b0, b1);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t g = row0 + ty * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int64_t g = row0 + ty * 8 + i;
     if (g >= rows) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int oc = col0 + tx * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+      const int oc = col0 + tx * 8 + j;
       if (oc < kout) Y[g * ldy + oc] = acc[i][j];
     }
   }
@@ -202,15 +229,26 @@ __device__ float block_sum_f(float v, float* red) {
   return red[32];
 }
 
-// One CTA of 1024 threads. A (k x lda, lda odd) in shared memory or in the
-// global scratch `gA`. G + s I = L L^T with s = 2^-20 * trace(G) / k, then
-// L^-1 in place, then Rinv = L^-T (upper) written row-major k x k.
-__global__ void __launch_bounds__(1024)
+// One CTA of kCholThreads threads. G + s I = R^T R with s = 2^-20 trace(G)/k
+// (shifted CholeskyQR: keeps the factorisation defined for a rank-deficient
+// block; X R^-1 then spans the same columns), then Rinv = R^-1.
+// A is k x lda (lda odd, so column walks hit distinct banks).
+//  - Cholesky, right-looking, one barrier per column: step j writes
+//    R[j][t] = L[t][j] into the upper triangle (never read by the update),
+//    R[j][j] into rdiag, and updates the trailing lower triangle with the
+//    scaled column computed on the fly.
+//  - Inverse, one barrier per row: R X = I is solved for all columns at once
+//    by back-substitution from the last row; the running right-hand sides B
+//    (upper triangular, B[i][c] stored at A[c][i]) take the freed lower
+//    triangle. Rinv[r][c] = B[r][c] / R[r][r].
+constexpr int kCholThreads = 256;
+
+__global__ void __launch_bounds__(kCholThreads)
     k_chol_inv(const float* __restrict__ G, int k, float* __restrict__ Rinv,
                float* __restrict__ gA, int* __restrict__ flags, int use_smem) {
   extern __shared__ float sh[];
   __shared__ float red[33];
-  __shared__ float temp_col[kMaxEll];
+  __shared__ float rdiag[kMaxEll];
   const int lda = k | 1;
   float* A = use_smem ? sh : gA;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -226,46 +264,40 @@ __global__ void __launch_bounds__(1024)
   const float shift = tr > 0.f ? ldexpf(tr / (float)k, -20) : 1e-30f;
   for (int i = tid; i < k; i += nt) A[i * lda + i] += shift;
   __syncthreads();
-  // right-looking Cholesky, lower triangle
   for (int j = 0; j < k; ++j) {
+    float p = A[j * lda + j];
+    if (!(p > 0.f)) p = shift;
+    const float ljj = sqrtf(p);
+    const float inv = 1.f / ljj;
     if (tid == 0) {
-      float p = A[j * lda + j];
-      if (!(p > 0.f)) {
-        p = shift;
-        atomicAdd(&flags[1], 1);
-      }
-      A[j * lda + j] = sqrtf(p);
+      rdiag[j] = ljj;
+      if (!(A[j * lda + j] > 0.f)) atomicAdd(&flags[1], 1);
     }
-    __syncthreads();
-    const float ljj = A[j * lda + j];
-    for (int i = j + 1 + tid; i < k; i += nt) A[i * lda + j] /= ljj;
-    __syncthreads();
+    for (int t = j + 1 + tid; t < k; t += nt) A[j * lda + t] = A[t * lda + j] * inv;
     for (int i = j + 1 + warp; i < k; i += nw) {
-      const float lij = A[i * lda + j];
-      for (int t = j + 1 + lane; t <= i; t += 32) A[i * lda + t] -= lij * A[t * lda + j];
+      const float lij = A[i * lda + j] * inv;
+      for (int t = j + 1 + lane; t <= i; t += 32) A[i * lda + t] -= lij * (A[t * lda + j] * inv);
     }
     __syncthreads();
   }
-  // L^-1 in place, last column first: Linv[i][j] = -Linv[j][j] * sum_{t=j+1..i} Linv[i][t] L[t][j]
-  for (int j = k - 1; j >= 0; --j) {
-    if (tid == 0) A[j * lda + j] = 1.f / A[j * lda + j];
-    __syncthreads();
-    for (int i = j + 1 + warp; i < k; i += nw) {
-      float s = 0.f;
-      for (int t = j + 1 + lane; t <= i; t += 32) s = fmaf(A[i * lda + t], A[t * lda + j], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) temp_col[i] = s;
+  // B = I in the lower triangle (B[i][c] at A[c][i], i <= c)
+  for (int e = tid; e < k * k; e += nt) {
+    int c = e / k, i = e % k;
+    if (i <= c) A[c * lda + i] = i == c ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int j = k - 1; j > 0; --j) {
+    const float rj = 1.f / rdiag[j];
+    // B[i][c] -= R[i][j] * B[j][c] / R[j][j]   for i < j <= c
+    for (int c = j + warp; c < k; c += nw) {
+      const float xjc = A[c * lda + j] * rj;
+      for (int i = lane; i < j; i += 32) A[c * lda + i] -= A[i * lda + j] * xjc;
     }
     __syncthreads();
-    const float dj = A[j * lda + j];
-    for (int i = j + 1 + tid; i < k; i += nt) A[i * lda + j] = -dj * temp_col[i];
-    __syncthreads();
   }
-  // Rinv = L^-T : Rinv[r][c] = Linv[c][r] for c >= r
   for (int e = tid; e < k * k; e += nt) {
     int r = e / k, c = e % k;
-    Rinv[e] = c >= r ? A[c * lda + r] : 0.f;
+    Rinv[e] = c >= r ? A[c * lda + r] / rdiag[r] : 0.f;
   }
 }
 
@@ -337,7 +369,7 @@ void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace
   const int n = map.total();
   const int ntiles = (n + kT - 1) / kT;
   const int npairs = ntiles * (ntiles + 1) / 2;
-  int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kR - 1) / kR, 640 / npairs));
+  int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kR - 1) / kR, kGramBlocks / npairs));
   int64_t rpc = (rows + nchunks - 1) / nchunks;
   rpc = ((rpc + kR - 1) / kR) * kR;
   nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
@@ -374,7 +406,7 @@ void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaS
                                   200 * 1024));
     attr_set |= 1u << dev;
   }
-  k_chol_inv<<<1, 1024, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags, use_smem);
+  k_chol_inv<<<1, kCholThreads, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags, use_smem);
   SFD_LAUNCH_CHECK();
 }
 

@@ -93,6 +93,40 @@ __device__ void tri_solve_scaled(const float* U0, const float* U1, const float* 
   for (int i = 0; i < n; ++i) Z[i * nwp] *= inv;
 }
 
+// LU with partial pivoting of the tridiagonal T - lam I (diagonal d, off
+// diagonal e): U has three diagonals (U0, U1, U2), Lm the multipliers, P the
+// row swaps; pivots below tiny_piv are raised to +-tiny_piv.
+__device__ void tri_factor(const float* d, const float* e, float lam, float* U0, float* U1,
+                           float* U2, float* Lm, float* P, int n, int st, float tiny_piv) {
+  float a_i = d[0] - lam, c_i = n > 1 ? e[0] : 0.f;
+  for (int i = 0; i + 1 < n; ++i) {
+    const float b = e[i];
+    const float an = d[i + 1] - lam;
+    const float cn = (i + 2 < n) ? e[i + 1] : 0.f;
+    float a_nx, c_nx;
+    if (fabsf(b) > fabsf(a_i)) {
+      const float l = a_i / b;
+      U0[i * st] = b; U1[i * st] = an; U2[i * st] = cn; P[i * st] = 1.f; Lm[i * st] = l;
+      a_nx = c_i - l * an;
+      c_nx = -l * cn;
+    } else {
+      float piv = a_i;
+      if (fabsf(piv) < tiny_piv) piv = piv < 0.f ? -tiny_piv : tiny_piv;
+      const float l = b / piv;
+      U0[i * st] = piv; U1[i * st] = c_i; U2[i * st] = 0.f; P[i * st] = 0.f; Lm[i * st] = l;
+      a_nx = an - l * c_i;
+      c_nx = cn;
+    }
+    a_i = a_nx;
+    c_i = c_nx;
+  }
+  U0[(n - 1) * st] = a_i;
+  for (int i = 0; i < n; ++i) {
+    float u = U0[i * st];
+    if (fabsf(u) < tiny_piv) U0[i * st] = u < 0.f ? -tiny_piv : tiny_piv;
+  }
+}
+
 struct EigWork {
   float* house;   // n * n : reflector k at house[k * n + i], i < n - k - 1
   float* beta;    // n
@@ -253,45 +287,36 @@ __global__ void __launch_bounds__(kThreads)
   // ------------------------------------------------ 3. inverse iteration
   const float pertol = 10.f * FLT_EPSILON * tnorm;
   const float tiny_piv = FLT_EPSILON * tnorm;
-  if (tid < nwant) {
-    const int j = tid;
-    // eigenvalues tied within fp32 resolution get distinct shifts
-    int rank = 0;
-    for (int k = j; k > 0 && wv[k - 1] - wv[k] < pertol; --k) ++rank;
-    const float lam = wv[j] - rank * pertol;
-    float* U0 = W.U0 + j; float* U1 = W.U1 + j; float* U2 = W.U2 + j;
-    float* Lm = W.Lm + j; float* Z = W.Z + j; float* P = W.piv + j;
-    float a_i = d[0] - lam, c_i = n > 1 ? e[0] : 0.f;
-    for (int i = 0; i + 1 < n; ++i) {
-      const float b = e[i];
-      const float an = d[i + 1] - lam;
-      const float cn = (i + 2 < n) ? e[i + 1] : 0.f;
-      float a_nx, c_nx;
-      if (fabsf(b) > fabsf(a_i)) {
-        const float l = a_i / b;
-        U0[i * nwp] = b; U1[i * nwp] = an; U2[i * nwp] = cn; P[i * nwp] = 1.f; Lm[i * nwp] = l;
-        a_nx = c_i - l * an;
-        c_nx = -l * cn;
-      } else {
-        float piv = a_i;
-        if (fabsf(piv) < tiny_piv) piv = piv < 0.f ? -tiny_piv : tiny_piv;
-        const float l = b / piv;
-        U0[i * nwp] = piv; U1[i * nwp] = c_i; U2[i * nwp] = 0.f; P[i * nwp] = 0.f; Lm[i * nwp] = l;
-        a_nx = an - l * c_i;
-        c_nx = cn;
+  {
+    // batches of eigenvectors whose factorisation and iterate fit in the A
+    // region (six vectors of n floats per eigenvector, interleaved by thread)
+    const int region = n * lda;
+    const int bsz = use_smem ? max(1, min(nwant, region / (6 * n))) : nwant;
+    for (int b0 = 0; b0 < nwant; b0 += bsz) {
+      const int j = b0 + tid;
+      if (tid < bsz && j < nwant) {
+        int rank = 0;  // eigenvalues tied within fp32 resolution get distinct shifts
+        for (int k = j; k > 0 && wv[k - 1] - wv[k] < pertol; --k) ++rank;
+        const float lam = wv[j] - rank * pertol;
+        float *U0, *U1, *U2, *Lm, *P, *Z;
+        int st;
+        if (use_smem) {
+          st = bsz;
+          U0 = A + tid; U1 = U0 + n * bsz; U2 = U1 + n * bsz; Lm = U2 + n * bsz;
+          P = Lm + n * bsz; Z = P + n * bsz;
+        } else {
+          st = nwp;
+          U0 = W.U0 + j; U1 = W.U1 + j; U2 = W.U2 + j; Lm = W.Lm + j; P = W.piv + j; Z = W.Z + j;
+        }
+        tri_factor(d, e, lam, U0, U1, U2, Lm, P, n, st, tiny_piv);
+        for (int i = 0; i < n; ++i) Z[i * st] = hash_unit(i, j);
+        for (int it = 0; it < 3; ++it) tri_solve_scaled(U0, U1, U2, Lm, P, Z, n, st);
+        if (use_smem)
+          for (int i = 0; i < n; ++i) W.Z[i * nwp + j] = Z[i * st];
       }
-      a_i = a_nx;
-      c_i = c_nx;
+      __syncthreads();
     }
-    U0[(n - 1) * nwp] = a_i;
-    for (int i = 0; i < n; ++i) {
-      float u = U0[i * nwp];
-      if (fabsf(u) < tiny_piv) U0[i * nwp] = u < 0.f ? -tiny_piv : tiny_piv;
-      Z[i * nwp] = hash_unit(i, j);
-    }
-    for (int it = 0; it < 3; ++it) tri_solve_scaled(U0, U1, U2, Lm, P, Z, n, nwp);
   }
-  __syncthreads();
   // eigenvectors into shared memory (or the global A region), column j contiguous
   float* Zs = A;
   for (int j = warp; j < nwant; j += nw)
@@ -336,7 +361,11 @@ __global__ void __launch_bounds__(kThreads)
       }
       // repair: one more solve with this vector's factorisation, then project again
       if (tid == 0) {
+        int rank = 0;
+        for (int k = j; k > 0 && wv[k - 1] - wv[k] < pertol; --k) ++rank;
         float* col = W.Z + j;
+        tri_factor(d, e, wv[j] - rank * pertol, W.U0 + j, W.U1 + j, W.U2 + j, W.Lm + j,
+                   W.piv + j, n, nwp, tiny_piv);
         for (int i = 0; i < n; ++i) col[i * nwp] = zj[i] + 1e-3f * hash_unit(i + 7919 * attempt, j);
         tri_solve_scaled(W.U0 + j, W.U1 + j, W.U2 + j, W.Lm + j, W.piv + j, col, n, nwp);
         for (int i = 0; i < n; ++i) zj[i] = col[i * nwp];

@@ -59,7 +59,7 @@ __global__ void k_check_entries(const int* __restrict__ idx, const float* __rest
       bad = 1;
       continue;
     }
-    atomicAdd(&col_count[c], 1);
+    if (col_count) atomicAdd(&col_count[c], 1);
     acc = fmaf(v, v, acc);
   }
   if (bad) atomicOr(&flags[0], 1);
@@ -86,6 +86,16 @@ __global__ void k_sum_doubles(const double* __restrict__ in, int n, double* __re
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = sh[0];
+}
+
+// every column index c in (keys[i-1], keys[i]] starts at position i
+__global__ void k_colptr_from_sorted(const int* __restrict__ keys, int64_t n, int d,
+                                     int* __restrict__ ptr) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const int prev = i == 0 ? -1 : keys[i - 1];
+  const int cur = i == n ? d : keys[i];
+  for (int c = prev + 1; c <= cur; ++c) ptr[c] = (int)i;
 }
 
 // -------------------------------------------------------------------- scans
@@ -281,7 +291,9 @@ __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* _
 
 // -------------------------------------------------------------- SpMM (k<=256)
 // One warp per work item; lane l owns float4 columns l, l+32 (VPL of them).
-template <int VPL>
+// Entries are read 32 at a time (coalesced) and broadcast by shuffles; U
+// gathers per lane are in flight at once.
+template <int VPL, int U>
 __global__ void __launch_bounds__(256)
     k_spmm(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
            const int2* __restrict__ items, const int* __restrict__ item_slot, int n_items,
@@ -297,48 +309,32 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int p = beg; p < end; p += 32) {
-    int cnt = min(32, end - p);
-    int c_l = lane < cnt ? idx[p + lane] : 0;
-    float v_l = lane < cnt ? val[p + lane] : 0.f;
-    int jj = 0;
-    for (; jj + 4 <= cnt; jj += 4) {
-      int c0 = __shfl_sync(0xffffffffu, c_l, jj);
-      int c1 = __shfl_sync(0xffffffffu, c_l, jj + 1);
-      int c2 = __shfl_sync(0xffffffffu, c_l, jj + 2);
-      int c3 = __shfl_sync(0xffffffffu, c_l, jj + 3);
-      float v0 = __shfl_sync(0xffffffffu, v_l, jj);
-      float v1 = __shfl_sync(0xffffffffu, v_l, jj + 1);
-      float v2 = __shfl_sync(0xffffffffu, v_l, jj + 2);
-      float v3 = __shfl_sync(0xffffffffu, v_l, jj + 3);
+    const int cnt = min(32, end - p);
+    const int c_l = lane < cnt ? idx[p + lane] : 0;
+    const float v_l = lane < cnt ? val[p + lane] : 0.f;
+    for (int jj = 0; jj < cnt; jj += U) {
+      int cu[U];
+      float vu[U];
 #pragma unroll
-      for (int q = 0; q < VPL; ++q) {
-        int vi = lane + 32 * q;
-        if (vi < nvec) {
-          float4 x0 = __ldg(&X[(int64_t)c0 * ldx4 + vi]);
-          float4 x1 = __ldg(&X[(int64_t)c1 * ldx4 + vi]);
-          float4 x2 = __ldg(&X[(int64_t)c2 * ldx4 + vi]);
-          float4 x3 = __ldg(&X[(int64_t)c3 * ldx4 + vi]);
-          acc[q].x = fmaf(v0, x0.x, acc[q].x); acc[q].y = fmaf(v0, x0.y, acc[q].y);
-          acc[q].z = fmaf(v0, x0.z, acc[q].z); acc[q].w = fmaf(v0, x0.w, acc[q].w);
-          acc[q].x = fmaf(v1, x1.x, acc[q].x); acc[q].y = fmaf(v1, x1.y, acc[q].y);
-          acc[q].z = fmaf(v1, x1.z, acc[q].z); acc[q].w = fmaf(v1, x1.w, acc[q].w);
-          acc[q].x = fmaf(v2, x2.x, acc[q].x); acc[q].y = fmaf(v2, x2.y, acc[q].y);
-          acc[q].z = fmaf(v2, x2.z, acc[q].z); acc[q].w = fmaf(v2, x2.w, acc[q].w);
-          acc[q].x = fmaf(v3, x3.x, acc[q].x); acc[q].y = fmaf(v3, x3.y, acc[q].y);
-          acc[q].z = fmaf(v3, x3.z, acc[q].z); acc[q].w = fmaf(v3, x3.w, acc[q].w);
-        }
+      for (int u = 0; u < U; ++u) {
+        // lanes past cnt carry value 0 and column 0: harmless multiply-adds
+        cu[u] = __shfl_sync(0xffffffffu, c_l, (jj + u) & 31);
+        vu[u] = jj + u < cnt ? __shfl_sync(0xffffffffu, v_l, (jj + u) & 31) : 0.f;
       }
-    }
-    for (; jj < cnt; ++jj) {
-      int c0 = __shfl_sync(0xffffffffu, c_l, jj);
-      float v0 = __shfl_sync(0xffffffffu, v_l, jj);
 #pragma unroll
       for (int q = 0; q < VPL; ++q) {
-        int vi = lane + 32 * q;
+        const int vi = lane + 32 * q;
         if (vi < nvec) {
-          float4 x0 = __ldg(&X[(int64_t)c0 * ldx4 + vi]);
-          acc[q].x = fmaf(v0, x0.x, acc[q].x); acc[q].y = fmaf(v0, x0.y, acc[q].y);
-          acc[q].z = fmaf(v0, x0.z, acc[q].z); acc[q].w = fmaf(v0, x0.w, acc[q].w);
+          float4 xs[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) xs[u] = __ldg(&X[(int64_t)cu[u] * ldx4 + vi]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            acc[q].x = fmaf(vu[u], xs[u].x, acc[q].x);
+            acc[q].y = fmaf(vu[u], xs[u].y, acc[q].y);
+            acc[q].z = fmaf(vu[u], xs[u].z, acc[q].z);
+            acc[q].w = fmaf(vu[u], xs[u].w, acc[q].w);
+          }
         }
       }
     }
@@ -427,6 +423,11 @@ void launch_check_entries(const int* idx, const float* val, int64_t nnz, int d, 
   SFD_LAUNCH_CHECK();
 }
 
+void colptr_from_sorted(const int* keys, int64_t n, int d, int* ptr, cudaStream_t s) {
+  k_colptr_from_sorted<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, d, ptr);
+  SFD_LAUNCH_CHECK();
+}
+
 void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_t s) {
   int nb = std::max(1, (n + kScanChunk - 1) / kScanChunk);
   k_scan_block_sums<<<nb, 1024, 0, s>>>(in, n, tmp);
@@ -503,13 +504,13 @@ void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float
   int grid = (w.n_items + 7) / 8;
   if (w.n_items > 0) {
     if (nvec <= 32)
-      k_spmm<1><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
-                                     (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                     (float4*)partial);
+      k_spmm<1, 8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
+                                        (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                        (float4*)partial);
     else
-      k_spmm<2><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
-                                     (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                     (float4*)partial);
+      k_spmm<2, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
+                                        (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                        (float4*)partial);
     SFD_LAUNCH_CHECK();
   }
   if (w.n_split > 0) {

@@ -17,7 +17,7 @@ namespace sfd {
 
 namespace {
 
-constexpr int kVsBlocks = 256;
+constexpr int kVsBlocks = 512;   // fixed grids: every reduction has a fixed order
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -76,24 +76,41 @@ __global__ void k_scale(float* __restrict__ x, int64_t n, const double* __restri
 }
 
 // wpart[b][c] = sum over the rows j of stripe b of Bt[j][c] * x[j]
-__global__ void k_btx_partial(const float* __restrict__ Bt, int ld, int ell, int64_t d,
-                              const float* __restrict__ x, float* __restrict__ wpart) {
+__global__ void __launch_bounds__(256)
+    k_btx_partial(const float* __restrict__ Bt, int ld, int ell, int64_t d,
+                  const float* __restrict__ x, float* __restrict__ wpart) {
   const int c = threadIdx.x;
   const int64_t rows = (d + gridDim.x - 1) / gridDim.x;
   const int64_t j0 = blockIdx.x * rows, j1 = min(d, j0 + rows);
-  float a = 0.f;
-  if (c < ell)
-    for (int64_t j = j0; j < j1; ++j) a = fmaf(Bt[j * ld + c], x[j], a);
-  if (c < ell) wpart[blockIdx.x * ell + c] = a;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  if (c < ell) {
+    int64_t j = j0;
+    for (; j + 4 <= j1; j += 4) {
+      a0 = fmaf(Bt[(j + 0) * ld + c], x[j + 0], a0);
+      a1 = fmaf(Bt[(j + 1) * ld + c], x[j + 1], a1);
+      a2 = fmaf(Bt[(j + 2) * ld + c], x[j + 2], a2);
+      a3 = fmaf(Bt[(j + 3) * ld + c], x[j + 3], a3);
+    }
+    for (; j < j1; ++j) a0 = fmaf(Bt[j * ld + c], x[j], a0);
+    wpart[blockIdx.x * ell + c] = (a0 + a1) + (a2 + a3);
+  }
 }
 
-__global__ void k_btx_reduce(const float* __restrict__ wpart, int nb, int ell,
-                             float* __restrict__ w) {
-  int c = threadIdx.x;
-  if (c >= ell) return;
+// w[c] = sum_b wpart[b][c] : one block per column c, fixed-order tree
+__global__ void __launch_bounds__(256)
+    k_btx_reduce(const float* __restrict__ wpart, int nb, int ell, float* __restrict__ w) {
+  const int c = blockIdx.x;
   float a = 0.f;
-  for (int b = 0; b < nb; ++b) a += wpart[b * ell + c];
-  w[c] = a;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += wpart[b * ell + c];
+  __shared__ float red[8];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    w[c] = t;
+  }
 }
 
 // v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block (fixed grid)
@@ -137,15 +154,20 @@ double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
   SFD_CUDA(cudaMemsetAsync(scal, 0, 4 * sizeof(double), s));
   launch_gauss_fill(x, a.d, 1, 1, a.seed, a.b, a.r, 2 /* tag of Alg. 6's x */, s);
   k_norm2_partial<<<kVsBlocks, 256, 0, s>>>(x, a.d, part);
+  SFD_LAUNCH_CHECK();
   k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, 1.0, 0, scal);
+  SFD_LAUNCH_CHECK();
   k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
   SFD_LAUNCH_CHECK();
   for (int t = 0; t < a.p; ++t) {
     spmv(*a.csr, x, u, ws.partial_rows, s);
     k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, ws.wpart);
-    k_btx_reduce<<<1, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
+    SFD_LAUNCH_CHECK();
+    k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
+    SFD_LAUNCH_CHECK();
     spmv(*a.csc, u, v, ws.partial_rows, s);
     k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
+    SFD_LAUNCH_CHECK();
     k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale, 1, scal);
     SFD_LAUNCH_CHECK();
     std::swap(x, v);

@@ -18,7 +18,7 @@ inline int ld_of(int k) { return (k + 7) & ~7; }
 
 constexpr int kMaxEll = 256;      // largest sketch size l
 constexpr int kMaxEig = 512;      // largest symmetric eigenproblem (2 l)
-constexpr int kSplit = 2048;      // entries per work item of the sparse products
+constexpr int kSplit = 256;       // entries per work item of the sparse products
 constexpr float kAlpha = 6.0f / 41.0f;  // alpha of Alg. 4
 
 struct CudaError {
@@ -93,10 +93,13 @@ struct Workspace {
 // ---------------------------------------------------------------- sparse ops
 // Row ids of each entry of a CSR (expand ptr).
 void launch_row_ids(const int* ptr, int nseg, int* rows, cudaStream_t s);
-// Validate a buffer slice: indices in [0,d), finite values; column counts
-// (atomic), sum of squares partials. Sets flags[0] on a bad index/value.
+// Validate a buffer slice: indices in [0,d), finite values; sum of squares
+// into fro2_out[0]; column counts (atomic) when col_count is not null. Sets
+// flags[0] on a bad index/value.
 void launch_check_entries(const int* idx, const float* val, int64_t nnz, int d, int* col_count,
                           double* fro2_out, int* flags, cudaStream_t s);
+// ptr[c] = first position of column c in the column-sorted keys (ptr[d] = n).
+void colptr_from_sorted(const int* keys, int64_t n, int d, int* ptr, cudaStream_t s);
 // Exclusive scan of n ints (n >= 0) into out[0..n]; out[n] = total.
 void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_t s);
 // Stable LSD radix sort of (key, a, b) by key in [0, 2^bits): CSR -> CSC.

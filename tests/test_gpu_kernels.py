@@ -147,4 +147,6 @@ def test_dense_shrink_matches_oracle(lib, rows, d, ell):
     got = B.cpu().numpy().astype(np.float64)
     ref = O.dense_shrink(M.astype(np.float64), ell)
     from oracle.metrics import bbt_rel_diff
-    assert bbt_rel_diff(got, ref) < 1e-5
+    # fp32 Gram + eigensolve of an n x n problem (n = rows): relative error ~ n u
+    tol = max(1e-5, 2 * rows * 2.0 ** -24)
+    assert bbt_rel_diff(got, ref) < tol
