@@ -187,6 +187,22 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
  * all device memory. */
 int sfd_symeig(int32_t n, const float* S, int32_t nwant, float* evals, float* evecs);
 
+/* The eigensolver of sfd_symeig without any allocation (no counterpart in the
+ * paper; this is a library service). For callers that must not let a library
+ * allocate device memory: a process whose caching allocator already holds the
+ * device's memory budget, or a latency-critical loop that cannot take the
+ * device-wide synchronisation cudaMalloc / cudaFree may cause. Its scratch is
+ * a fixed array inside libsfd.so (~2.1 MB, held on every GPU that loads the
+ * library until the process exits), so n <= 256 (1 <= nwant <= n); larger n
+ * returns SFD_EINVAL. S, evals, evecs are caller-owned device memory as in
+ * sfd_symeig. Runs on the legacy default stream (0) of the current device and
+ * returns after that stream has finished. The first call on each device looks
+ * up the array's device address; make that first call before any stream
+ * capture. All calls share the one array: calls that overlap on the GPU (from
+ * several host threads or streams) race and must be serialised by the caller.
+ * Errors: SFD_EINVAL, SFD_ECUDA. */
+int sfd_symeig_noalloc(int32_t n, const float* S, int32_t nwant, float* evals, float* evecs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,7 +50,8 @@ class sfd_shrink_info(ctypes.Structure):
 
 EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "sfd_merge",
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
-           "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig"]
+           "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig",
+           "sfd_symeig_noalloc"]
 
 _lib = None
 
@@ -86,6 +87,7 @@ def load(path=None):
     L.sfd_csr_spmm.argtypes = [i64, i64, vp, vp, vp, i32, vp, i32, vp, i32, i32]
     L.sfd_orthonormalize.argtypes = [i64, i32, vp, i32]
     L.sfd_symeig.argtypes = [i32, vp, i32, vp, vp]
+    L.sfd_symeig_noalloc.argtypes = [i32, vp, i32, vp, vp]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error"):
@@ -213,6 +215,13 @@ def sfd_orthonormalize(rows, k, X, ld):
 def sfd_symeig(n, S, nwant, evals, evecs):
     _check(load().sfd_symeig(n, ctypes.c_void_p(S.data_ptr()), nwant,
                              ctypes.c_void_p(evals.data_ptr()), ctypes.c_void_p(evecs.data_ptr())))
+
+
+def sfd_symeig_noalloc(n, S, nwant, evals, evecs):
+    """Same eigensolver, scratch in the library's fixed array (no allocation)."""
+    _check(load().sfd_symeig_noalloc(n, ctypes.c_void_p(S.data_ptr()), nwant,
+                                     ctypes.c_void_p(evals.data_ptr()),
+                                     ctypes.c_void_p(evecs.data_ptr())))
 
 
 class SFD:
