@@ -18,9 +18,11 @@
  *    memory of the current CUDA device). Caller arrays stay the caller's; the
  *    library copies what it keeps before the call returns.
  *  - Dense matrices are row-major float32 with the leading dimension stated.
- *  - A context is bound to the CUDA device current at sfd_create and runs on
- *    one CUDA stream (options.cuda_stream, or a stream it creates). Calls on
- *    one context must not overlap; distinct contexts are independent.
+ *  - A context is bound to the CUDA device current at sfd_create. Its work is
+ *    ordered after the work already queued on options.cuda_stream when a call
+ *    starts, and that stream waits for the call's work before the call returns
+ *    (internally a context runs several streams). Calls on one context must
+ *    not overlap; distinct contexts are independent.
  *  - Every call returns with its work finished on the device (results
  *    written, stream synchronised), except where stated.
  */
@@ -63,6 +65,8 @@ typedef struct sfd_options {
   int32_t inject_vs_fail; /* testing: force this many VerifySpectral verdicts to False (host-side) */
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the context creates its own */
   int32_t profile;      /* 1: time every sparse-product launch with CUDA events (sfd_stats.spmm_*) */
+  int32_t slots;        /* buffers in flight: each slot runs one buffer's BoostedSparseShrink on its
+                           own stream while DenseShrink folds finished buffers in order; 0: 3 */
 } sfd_options;
 
 /* Counters of a context (Alg. 2 / Alg. 4 bookkeeping). */

@@ -1,0 +1,115 @@
+// Device-side engine of Sparse Frequent Directions (internal, not the C ABI).
+//
+// A Slot owns everything one buffer's BoostedSparseShrink needs (Alg. 3, 4,
+// 1, 6): the CSR and CSC copies of A', the work lists, the dense blocks of
+// SimultaneousIteration, B'^T, scratch, a CUDA stream and pinned memory for
+// the verdict. Several slots run different buffers concurrently, so the
+// one-CTA steps (Cholesky, eigensolver) of one buffer overlap the
+// whole-GPU steps (sparse products, Grams) of another.
+//
+// The Merger owns the sketch B (as B^T, d x ld, ping-pong pair) and runs
+// DenseShrink (Alg. 5) on its own stream, in buffer order.
+//
+// Nothing on a slot's stream synchronises the host: counts, norms, Delta and
+// the VerifySpectral verdict stay on the device until the verdict is copied
+// to pinned host memory at the end of an attempt.
+#pragma once
+
+#include <vector>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+
+// Device allocations of one owner, freed together.
+struct DevArena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) throw CudaError{e, "cudaMalloc"};
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// Scratch of the dense stages (Gram, Cholesky, eigensolver, weights).
+void alloc_dense_scratch(DevArena& A, Workspace& ws);
+
+struct Slot {
+  int64_t d = 0, cap_rows = 0, cap_nnz = 0;
+  int ell = 0, ld = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t done = nullptr;   // recorded after the verdict copy of an attempt
+  cudaEvent_t freed = nullptr;  // recorded on the merge stream after DenseShrink read B'^T
+  bool freed_pending = false;   // `freed` has been recorded and not yet waited on
+  DevArena arena;
+  Csr csr, csc;
+  int *key = nullptr, *key2 = nullptr, *a_alt = nullptr;
+  float* b_alt = nullptr;
+  float *W = nullptr, *W2 = nullptr, *Y = nullptr, *Y2 = nullptr;
+  float* Bpt = nullptr;         // B'^T, d x ld
+  Workspace ws;
+  double* fro2 = nullptr;       // [0] ||A'||_F^2, [1..] partials
+  Verdict* verdict_dev = nullptr;
+  Verdict* verdict_host = nullptr;  // pinned
+  int* ptr_host = nullptr;          // pinned staging of the local row pointer
+  // profiling of the sparse products
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, double>> ev_pending;
+  int ev_used = 0;
+  int64_t prof_launches = 0;
+  double prof_ms = 0, prof_bytes = 0;
+
+  Slot(int64_t d, int ell, int64_t cap_rows, int64_t cap_nnz, cudaStream_t s);
+  ~Slot();
+  Slot(const Slot&) = delete;
+  Slot& operator=(const Slot&) = delete;
+
+  // the stream must not overwrite B'^T before DenseShrink has read it
+  void wait_freed();
+  // CSR structure + CSC copy + work lists of the buffer already in csr.{ptr,idx,val}
+  void build(int m, int64_t nnz);
+  // One SparseShrink attempt (Alg. 3) + Delta + VerifySpectral (Alg. 6) +
+  // verdict copy; `done` is recorded at the end.
+  void enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify);
+  void collect_profile();  // host: needs `done`
+
+ private:
+  void cleanup();
+  void orth_pass(const float* X, int64_t rows, float* Xout);
+  void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in);
+};
+
+struct Merger {
+  int64_t d = 0;
+  int ell = 0, ld = 0;
+  cudaStream_t stream = nullptr;
+  DevArena arena;
+  float* Bt[2] = {nullptr, nullptr};  // d x ld
+  int cur = 0;
+  Workspace ws;
+
+  Merger(int64_t d, int ell);
+  ~Merger();
+  Merger(const Merger&) = delete;
+  Merger& operator=(const Merger&) = delete;
+
+  float* B() { return Bt[cur]; }
+  void zero();
+  // B <- DenseShrink([B; X]) with X^T given as d x k1 (leading dimension ldx).
+  void dense_shrink(const float* Xt, int ldx, int k1);
+
+ private:
+  void cleanup();
+};
+
+}  // namespace sfd

@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(256, 2)
       const int rr = li / kT, cc = li % kT;
       const int64_t g = r0 + rr;
       const int ca = ti * kT + cc;
-      As[rr][cc] = (g < r_end && ca < n) ? X[g * ldx + map.col(ca)] : 0.f;
+      As[rr][cc] = (g < r_end && ca < n) ? map.at(X, ldx, g, ca) : 0.f;
       if (!diag) {
         const int cb = tj * kT + cc;
-        Bs[rr][cc] = (g < r_end && cb < n) ? X[g * ldx + map.col(cb)] : 0.f;
+        Bs[rr][cc] = (g < r_end && cb < n) ? map.at(X, ldx, g, cb) : 0.f;
       }
     }
     __syncthreads();
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, 2)
       const int rr = li / kR, cc = li % kR;     // X tile: 128 rows x 16 inner
       const int64_t g = row0 + rr;
       const int c = c0 + cc;
-      Xs[cc][rr] = (g < rows && c < n) ? X[g * ldx + map.col(c)] : 0.f;
+      Xs[cc][rr] = (g < rows && c < n) ? map.at(X, ldx, g, c) : 0.f;
       const int tr = li / kT, tc = li % kT;     // T tile: 16 inner x 128 out
       const int cr = c0 + tr, oc = col0 + tc;
       Ts[tr][tc] = (cr < n && oc < kout) ? T[(int64_t)cr * kout + oc] : 0.f;
@@ -301,6 +301,158 @@ __global__ void __launch_bounds__(kCholThreads)
   }
 }
 
+// Register-tiled Cholesky + inverse for k <= 128: 16 x 16 threads, element
+// (i, t) lives in thread (i % 16, t % 16), register (i / 16, t / 16) (cyclic,
+// so every thread keeps work as the factorisation shrinks). One barrier per
+// step: step j publishes the raw column j (and its pivot) into one of two
+// shared buffers; every thread scales on the fly, so the next step can fill
+// the other buffer while slow threads still read this one.
+//  - Cholesky: A[i][t] -= c_i c_t / c_j for j < t <= i (c = raw column j),
+//    L[i][j] = c_i / sqrt(c_j) kept in shared memory for the inverse.
+//  - Inverse: forward substitution L X = I on all columns at once with the
+//    right-hand sides in registers; Rinv = X^T.
+template <int TL>
+__device__ __forceinline__ float sel_reg(const float (&a)[TL][TL], int p, int q) {
+  float v = 0.f;
+#pragma unroll
+  for (int pp = 0; pp < TL; ++pp)
+#pragma unroll
+    for (int qq = 0; qq < TL; ++qq)
+      if (pp == p && qq == q) v = a[pp][qq];
+  return v;
+}
+
+template <int TL>
+__global__ void __launch_bounds__(256)
+    k_chol_inv_reg(const float* __restrict__ G, int k, float* __restrict__ Rinv,
+                   int* __restrict__ flags) {
+  extern __shared__ float Lsm[];        // L[i][j] at Lsm[j * LS + i] (column j contiguous)
+  __shared__ float buf[2][129];         // raw column / row, slot 128 holds the pivot
+  __shared__ float red[33];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const int LS = k + 1;
+  float a[TL][TL];
+  float tr = 0.f;
+#pragma unroll
+  for (int p = 0; p < TL; ++p)
+#pragma unroll
+    for (int q = 0; q < TL; ++q) {
+      const int i = ty + 16 * p, t = tx + 16 * q;
+      const float v = (i < k && t < k) ? G[i * k + t] : 0.f;
+      a[p][q] = v;
+      if (i == t && i < k) tr += v;
+    }
+  tr = block_sum_f(tr, red);
+  const float shift = tr > 0.f ? ldexpf(tr / (float)k, -20) : 1e-30f;
+#pragma unroll
+  for (int p = 0; p < TL; ++p)
+#pragma unroll
+    for (int q = 0; q < TL; ++q)
+      if (ty + 16 * p == tx + 16 * q) a[p][q] += shift;
+  // ------------------------------------------------------------ Cholesky
+  for (int j = 0; j < k; ++j) {
+    const int rj = j & 15, qj = j >> 4;
+    float* col = buf[j & 1];
+    if (tx == rj) {
+#pragma unroll
+      for (int p = 0; p < TL; ++p) {
+        const int i = ty + 16 * p;
+        float v = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < TL; ++qq)
+          if (qq == qj) v = a[p][qq];
+        if (i >= j && i < k) col[i] = v;
+        if (i == j) {
+          float piv = v;
+          if (!(piv > 0.f)) {
+            piv = shift;
+            atomicAdd(&flags[1], 1);
+          }
+          col[128] = piv;
+        }
+      }
+    }
+    __syncthreads();
+    const float piv = col[128];
+    const float rinv = 1.f / piv;
+    float ci[TL], ct[TL];
+#pragma unroll
+    for (int p = 0; p < TL; ++p) {
+      const int i = ty + 16 * p;
+      ci[p] = (i > j && i < k) ? col[i] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < TL; ++q) {
+      const int t = tx + 16 * q;
+      ct[q] = (t > j && t < k) ? col[t] * rinv : 0.f;
+    }
+#pragma unroll
+    for (int p = 0; p < TL; ++p)
+#pragma unroll
+      for (int q = 0; q < TL; ++q) a[p][q] = fmaf(-ci[p], ct[q], a[p][q]);
+    if (tx == rj) {
+      const float rs = rsqrtf(piv);
+#pragma unroll
+      for (int p = 0; p < TL; ++p) {
+        const int i = ty + 16 * p;
+        if (i > j && i < k) Lsm[j * LS + i] = col[i] * rs;
+      }
+    }
+    if (tid == 0) Lsm[j * LS + j] = sqrtf(piv);
+  }
+  __syncthreads();
+  // ------------------------------------------- inverse: L X = I, B in a[][]
+#pragma unroll
+  for (int p = 0; p < TL; ++p)
+#pragma unroll
+    for (int q = 0; q < TL; ++q) a[p][q] = (ty + 16 * p == tx + 16 * q) ? 1.f : 0.f;
+  for (int j = 0; j < k; ++j) {
+    const int rj = j & 15, qj = j >> 4;
+    float* row = buf[j & 1];
+    const float ljj_inv = 1.f / Lsm[j * LS + j];
+    if (ty == rj) {
+#pragma unroll
+      for (int q = 0; q < TL; ++q) {
+        const int c = tx + 16 * q;
+        float v = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < TL; ++pp)
+          if (pp == qj) v = a[pp][q];
+        if (c <= j) row[c] = v;
+        // row j is final: X[j][c] = B[j][c] / L[j][j]
+#pragma unroll
+        for (int pp = 0; pp < TL; ++pp)
+          if (pp == qj) a[pp][q] = v * ljj_inv;
+      }
+    }
+    __syncthreads();
+    float li[TL], rc[TL];
+#pragma unroll
+    for (int p = 0; p < TL; ++p) {
+      const int i = ty + 16 * p;
+      li[p] = (i > j && i < k) ? Lsm[j * LS + i] * ljj_inv : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < TL; ++q) {
+      const int c = tx + 16 * q;
+      rc[q] = c <= j ? row[c] : 0.f;
+    }
+#pragma unroll
+    for (int p = 0; p < TL; ++p)
+#pragma unroll
+      for (int q = 0; q < TL; ++q) a[p][q] = fmaf(-li[p], rc[q], a[p][q]);
+  }
+  // Rinv = X^T : Rinv[c][i] = X[i][c] for c <= i
+#pragma unroll
+  for (int p = 0; p < TL; ++p)
+#pragma unroll
+    for (int q = 0; q < TL; ++q) {
+      const int i = ty + 16 * p, c = tx + 16 * q;
+      if (i < k && c < k) Rinv[c * k + i] = c <= i ? a[p][q] : 0.f;
+    }
+}
+
 // ------------------------------------------------------- shrink weights
 __global__ void k_shrink_weights(const float* __restrict__ evals, const float* __restrict__ evecs,
                                  int n, int nwant, int nkeep, int thr_zero,
@@ -395,6 +547,36 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
 }
 
 void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s) {
+  if (k <= 128) {
+    static unsigned reg_attr = 0;  // one bit per device
+    int dv = 0;
+    SFD_CUDA(cudaGetDevice(&dv));
+    const int bytes_max = 128 * 129 * (int)sizeof(float);
+    if (dv < 32 && !(reg_attr & (1u << dv))) {
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
+      reg_attr |= 1u << dv;
+    }
+    const size_t bytes = (size_t)k * (k + 1) * sizeof(float);
+    switch ((k + 15) / 16) {
+      case 1: k_chol_inv_reg<1><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 2: k_chol_inv_reg<2><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 3: k_chol_inv_reg<3><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 4: k_chol_inv_reg<4><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 5: k_chol_inv_reg<5><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 6: k_chol_inv_reg<6><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      case 7: k_chol_inv_reg<7><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+      default: k_chol_inv_reg<8><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
+    }
+    SFD_LAUNCH_CHECK();
+    return;
+  }
   const int lda = k | 1;
   size_t bytes = (size_t)k * lda * sizeof(float);
   int use_smem = bytes <= 200 * 1024;

@@ -397,6 +397,151 @@ __global__ void __launch_bounds__(kThreads)
   for (int j = tid; j < nwant; j += nt) evals[j] = wv[j];
 }
 
+// ---------------------------------------------------------------------------
+// PSD input, n <= kJacobiMax: one-sided Jacobi on the Cholesky factor.
+// S + s I = L L^T (s = 2^-20 trace/n keeps a rank-deficient Gram factorable).
+// Orthogonalising the columns of L by plane rotations (Hestenes) gives
+// L J = U Sigma with U the eigenvectors of L L^T and Sigma^2 its eigenvalues,
+// so no rotation product is accumulated: eigenvector i is column i / its norm,
+// eigenvalue i its squared norm minus s. Pairs follow the round-robin
+// tournament; one warp per pair, one barrier per round. Column walks are
+// bank-conflict free because the row stride n|1 is odd.
+constexpr int kJacobiMax = 64;   // measured: faster than the tridiagonal path only up to ~64
+constexpr int kJacobiSweeps = 30;
+
+__global__ void __launch_bounds__(kThreads)
+    k_symeig_jacobi(const float* __restrict__ S, int n, int nwant, float* __restrict__ evals,
+                    float* __restrict__ evecs) {
+  extern __shared__ float A[];          // n x (n|1)
+  __shared__ float nrm[kJacobiMax + 1], rdiag[kJacobiMax];
+  __shared__ int rnk[kJacobiMax];
+  __shared__ float red[33];
+  __shared__ int rotations;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int lda = n | 1;
+  // shift: 2^-20 trace/n for a positive semi-definite S (the Grams of the
+  // method); if the factorisation meets a non-positive pivot, S is indefinite
+  // and it restarts with the Gershgorin bound, which makes S + sI definite
+  __shared__ int indefinite;
+  __shared__ float shift_sh;
+  float tr = 0.f, gersh = FLT_MAX;
+  for (int i = warp; i < n; i += nw) {
+    float off = 0.f;
+    for (int j = lane; j < n; j += 32) {
+      const float v = S[(size_t)i * n + j];
+      if (j == i) tr += v; else off += fabsf(v);
+    }
+    off = warp_sum(off);
+    if (lane == 0) gersh = fminf(gersh, S[(size_t)i * n + i] - off);
+  }
+  tr = block_reduce(tr, red, 0);
+  gersh = block_reduce(gersh, red, 2);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (tid == 0) {
+      float sft = tr > 0.f ? ldexpf(tr / (float)n, -20) : FLT_MIN;
+      if (attempt == 1) sft = fmaxf(sft, -gersh) * 1.01f + FLT_MIN;
+      shift_sh = sft;
+      indefinite = 0;
+    }
+    __syncthreads();
+    const float sft = shift_sh;
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e % n;
+      A[i * lda + j] = S[e] + (i == j ? sft : 0.f);
+    }
+    __syncthreads();
+    // Cholesky, lower, in place; column j is scaled one step later (after the
+    // barrier), so the trailing update can read it raw in the same step
+    for (int j = 0; j < n; ++j) {
+      float piv = A[j * lda + j];
+      if (!(piv > 0.f)) {
+        piv = sft;
+        if (tid == 0 && attempt == 0 && j < n) indefinite = 1;
+      }
+      const float rinv = 1.f / piv;
+      if (tid == 0) rdiag[j] = sqrtf(piv);
+      if (j > 0) {
+        const float sc = 1.f / rdiag[j - 1];
+        for (int i = j + tid; i < n; i += nt) A[i * lda + (j - 1)] *= sc;
+      }
+      for (int i = j + 1 + warp; i < n; i += nw) {
+        const float aij = A[i * lda + j] * rinv;
+        for (int t = j + 1 + lane; t <= i; t += 32) A[i * lda + t] -= aij * A[t * lda + j];
+      }
+      __syncthreads();
+    }
+    if (!indefinite) break;
+  }
+  const float shift = shift_sh;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    if (j > i) A[i * lda + j] = 0.f;
+    else if (j == i) A[i * lda + j] = rdiag[i];
+  }
+  __syncthreads();
+  // one-sided Jacobi over the columns of L
+  const int np = n + (n & 1);                 // even count; column n is a virtual zero
+  const float tiny = ldexpf(fabsf(tr) + shift * n, -30);  // columns below this are zero
+  const float tol = 4.f * FLT_EPSILON * sqrtf((float)n);  // attainable fp32 orthogonality
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    if (tid == 0) rotations = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int w = warp; w < np / 2; w += nw) {
+        int p, q;
+        if (w == 0) { p = r; q = np - 1; }
+        else { p = (r + w) % (np - 1); q = (r - w + (np - 1)) % (np - 1); }
+        if (p >= n || q >= n) continue;
+        float a = 0.f, b = 0.f, g = 0.f;
+        for (int i = lane; i < n; i += 32) {
+          const float x = A[i * lda + p], y = A[i * lda + q];
+          a = fmaf(x, x, a);
+          b = fmaf(y, y, b);
+          g = fmaf(x, y, g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (fminf(a, b) <= tiny || fabsf(g) <= tol * sqrtf(a * b)) continue;
+        const float zeta = (b - a) / (2.f * g);
+        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float c = rsqrtf(1.f + t * t), sn = c * t;
+        for (int i = lane; i < n; i += 32) {
+          const float x = A[i * lda + p], y = A[i * lda + q];
+          A[i * lda + p] = c * x - sn * y;
+          A[i * lda + q] = sn * x + c * y;
+        }
+        if (lane == 0) atomicAdd(&rotations, 1);
+      }
+      __syncthreads();
+    }
+    if (rotations == 0) break;
+    __syncthreads();
+  }
+  // squared column norms, ranks (descending, ties by index), outputs
+  for (int c = warp; c < n; c += nw) {
+    float a = 0.f;
+    for (int i = lane; i < n; i += 32) a = fmaf(A[i * lda + c], A[i * lda + c], a);
+    a = warp_sum(a);
+    if (lane == 0) nrm[c] = a;
+  }
+  __syncthreads();
+  for (int c = tid; c < n; c += nt) {
+    int r = 0;
+    const float v = nrm[c];
+    for (int c2 = 0; c2 < n; ++c2) r += (nrm[c2] > v) || (nrm[c2] == v && c2 < c);
+    rnk[c] = r;
+  }
+  __syncthreads();
+  for (int c = warp; c < n; c += nw) {
+    const int r = rnk[c];
+    if (r >= nwant) continue;
+    const float v = nrm[c];
+    const float inv = v > 0.f ? rsqrtf(v) : 0.f;
+    for (int i = lane; i < n; i += 32) evecs[(size_t)i * nwant + r] = A[i * lda + c] * inv;
+    if (lane == 0) evals[r] = v - shift;
+  }
+}
+
 }  // namespace
 
 size_t symeig_work_floats(int n, int nwant) {
@@ -406,7 +551,21 @@ size_t symeig_work_floats(int n, int nwant) {
 }
 
 void symeig(const float* S, int n, int nwant, float* evals, float* evecs, float* work,
-            cudaStream_t s) {
+            cudaStream_t s, bool psd) {
+  if (psd && n <= kJacobiMax) {
+    static unsigned jac_attr = 0;  // one bit per device
+    int dv = 0;
+    SFD_CUDA(cudaGetDevice(&dv));
+    if (dv < 32 && !(jac_attr & (1u << dv))) {
+      SFD_CUDA(cudaFuncSetAttribute(k_symeig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kJacobiMax * (kJacobiMax | 1) * (int)sizeof(float)));
+      jac_attr |= 1u << dv;
+    }
+    const size_t bytes = (size_t)n * (n | 1) * sizeof(float);
+    k_symeig_jacobi<<<1, kThreads, bytes, s>>>(S, n, nwant, evals, evecs);
+    SFD_LAUNCH_CHECK();
+    return;
+  }
   const int lda = n | 1;
   size_t bytes = (size_t)n * lda * sizeof(float);
   int use_smem = bytes <= (size_t)kSmemLimit;

@@ -296,12 +296,12 @@ __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* _
 template <int VPL, int U>
 __global__ void __launch_bounds__(256)
     k_spmm(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
-           const int2* __restrict__ items, const int* __restrict__ item_slot, int n_items,
-           const float4* __restrict__ X, int ldx4, int nvec, float4* __restrict__ Y, int ldy4,
-           float4* __restrict__ partial) {
+           const int2* __restrict__ items, const int* __restrict__ item_slot,
+           const int* __restrict__ n_items_ptr, const float4* __restrict__ X, int ldx4, int nvec,
+           float4* __restrict__ Y, int ldy4, float4* __restrict__ partial) {
   int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (item >= n_items) return;
+  if (item >= *n_items_ptr) return;
   int2 it = items[item];
   int seg = it.x, beg = it.y;
   int end = min(beg + kSplit, ptr[seg + 1]);
@@ -350,12 +350,12 @@ __global__ void __launch_bounds__(256)
 
 template <int VPL>
 __global__ void k_spmm_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
-                             const int* __restrict__ split_count, int n_split,
+                             const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
                              const float4* __restrict__ partial, int ldy4, int nvec,
                              float4* __restrict__ Y) {
   int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (w >= n_split) return;
+  if (w >= *n_split_ptr) return;
   int seg = split_seg[w], f = split_first[w], c = split_count[w];
 #pragma unroll
   for (int q = 0; q < VPL; ++q) {
@@ -373,11 +373,12 @@ __global__ void k_spmm_fixup(const int* __restrict__ split_seg, const int* __res
 // ------------------------------------------------------------------- SpMV
 __global__ void __launch_bounds__(256)
     k_spmv(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
-           const int2* __restrict__ items, const int* __restrict__ item_slot, int n_items,
-           const float* __restrict__ x, float* __restrict__ y, float* __restrict__ partial) {
+           const int2* __restrict__ items, const int* __restrict__ item_slot,
+           const int* __restrict__ n_items_ptr, const float* __restrict__ x, float* __restrict__ y,
+           float* __restrict__ partial) {
   int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (item >= n_items) return;
+  if (item >= *n_items_ptr) return;
   int2 it = items[item];
   int seg = it.x, beg = it.y;
   int end = min(beg + kSplit, ptr[seg + 1]);
@@ -394,10 +395,10 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void k_spmv_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
-                             const int* __restrict__ split_count, int n_split,
+                             const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
                              const float* __restrict__ partial, float* __restrict__ y) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= n_split) return;
+  if (w >= *n_split_ptr) return;
   float a = 0.f;
   for (int t = 0; t < split_count[w]; ++t) a += partial[split_first[w] + t];
   y[split_seg[w]] = a;
@@ -463,34 +464,26 @@ void radix_sort_by_key(int* key, int* a, float* b, int* key_alt, int* a_alt, flo
 void build_work(Csr& c, cudaStream_t s) {
   SegWork& w = c.work;
   int n = c.nseg;
-  if (n <= 0) {
-    w.n_items = w.n_split = w.n_slots = 0;
-    return;
-  }
-  // counts in split_seg/split_first/split_count scratch, offsets into item_slot area
-  int* cnt_items = w.split_seg;     // reused as scratch before fill
-  int* cnt_slots = w.split_first;
-  int* cnt_split = w.split_count;
-  k_count_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, cnt_items, cnt_slots, cnt_split);
-  SFD_LAUNCH_CHECK();
-  int* off = w.counters + 8;  // 3 * (n + 1) ints of offsets
+  int* off = w.counters + 8;  // 3 * (n + 1) ints of offsets, then scan scratch
   int* item_off = off;
   int* slot_off = off + (n + 1);
   int* split_off = off + 2 * (n + 1);
   int* tmp = off + 3 * (n + 1);
+  w.d_n_items = item_off + n;
+  w.d_n_split = split_off + n;
+  if (n <= 0) {
+    SFD_CUDA(cudaMemsetAsync(off, 0, 3 * sizeof(int), s));
+    return;
+  }
+  // counts in split_seg/split_first/split_count scratch (filled after the scans)
+  int* cnt_items = w.split_seg;
+  int* cnt_slots = w.split_first;
+  int* cnt_split = w.split_count;
+  k_count_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, cnt_items, cnt_slots, cnt_split);
+  SFD_LAUNCH_CHECK();
   exclusive_scan(cnt_items, n, item_off, tmp, s);
   exclusive_scan(cnt_slots, n, slot_off, tmp, s);
   exclusive_scan(cnt_split, n, split_off, tmp, s);
-  int h[3];
-  SFD_CUDA(cudaMemcpyAsync(&h[0], item_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SFD_CUDA(cudaMemcpyAsync(&h[1], split_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SFD_CUDA(cudaMemcpyAsync(&h[2], slot_off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SFD_CUDA(cudaStreamSynchronize(s));
-  w.n_items = h[0];
-  w.n_split = h[1];
-  w.n_slots = h[2];
-  if (w.n_items > w.cap_items) throw CudaError{cudaErrorMemoryAllocation, "work list capacity"};
-  // the counts scratch aliases split_*: copy offsets first is not needed, fill reads offsets only
   k_fill_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, item_off, slot_off, split_off, w.items,
                                                w.item_slot, w.split_seg, w.split_first,
                                                w.split_count);
@@ -500,43 +493,35 @@ void build_work(Csr& c, cudaStream_t s) {
 void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
           cudaStream_t s) {
   const SegWork& w = c.work;
-  int nvec = (k + 3) / 4;
-  int grid = (w.n_items + 7) / 8;
-  if (w.n_items > 0) {
-    if (nvec <= 32)
-      k_spmm<1, 8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
-                                        (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                        (float4*)partial);
-    else
-      k_spmm<2, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.n_items,
-                                        (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                        (float4*)partial);
-    SFD_LAUNCH_CHECK();
-  }
-  if (w.n_split > 0) {
-    int g2 = (w.n_split + 7) / 8;
-    if (nvec <= 32)
-      k_spmm_fixup<1><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.n_split,
-                                         (const float4*)partial, ldy / 4, nvec, (float4*)Y);
-    else
-      k_spmm_fixup<2><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.n_split,
-                                         (const float4*)partial, ldy / 4, nvec, (float4*)Y);
-    SFD_LAUNCH_CHECK();
-  }
+  const int nvec = (k + 3) / 4;
+  const int grid = (w.cap_items + 7) / 8;
+  if (nvec <= 32)
+    k_spmm<1, 8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                      (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                      (float4*)partial);
+  else
+    k_spmm<2, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                      (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
+                                      (float4*)partial);
+  SFD_LAUNCH_CHECK();
+  const int g2 = (w.cap_split + 7) / 8;
+  if (nvec <= 32)
+    k_spmm_fixup<1><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split,
+                                       (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+  else
+    k_spmm_fixup<2><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split,
+                                       (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+  SFD_LAUNCH_CHECK();
 }
 
 void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s) {
   const SegWork& w = c.work;
-  if (w.n_items > 0) {
-    k_spmv<<<(w.n_items + 7) / 8, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
-                                               w.n_items, x, y, partial);
-    SFD_LAUNCH_CHECK();
-  }
-  if (w.n_split > 0) {
-    k_spmv_fixup<<<(w.n_split + 127) / 128, 128, 0, s>>>(w.split_seg, w.split_first,
-                                                         w.split_count, w.n_split, partial, y);
-    SFD_LAUNCH_CHECK();
-  }
+  k_spmv<<<(w.cap_items + 7) / 8, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
+                                               w.d_n_items, x, y, partial);
+  SFD_LAUNCH_CHECK();
+  k_spmv_fixup<<<(w.cap_split + 127) / 128, 128, 0, s>>>(w.split_seg, w.split_first,
+                                                         w.split_count, w.d_n_split, partial, y);
+  SFD_LAUNCH_CHECK();
 }
 
 }  // namespace sfd

@@ -43,8 +43,9 @@ __global__ void k_norm2_partial(const float* __restrict__ x, int64_t n, float* _
 }
 
 // scal[0] logsum, scal[1] inverse norm of the current x, scal[2] 1 if some C x_t was 0.
-// mode 0: initial normalisation (no log term); mode 1: a power step with factor `scale`.
-__global__ void k_norm_finalize(const float* __restrict__ part, int nb, double scale, int mode,
+// mode 0: initial normalisation (no log term); mode 1: a power step with factor *scale.
+__global__ void k_norm_finalize(const float* __restrict__ part, int nb,
+                                const double* __restrict__ scale_ptr, int mode,
                                 double* __restrict__ scal) {
   __shared__ double sh[256];
   double a = 0.0;
@@ -59,7 +60,7 @@ __global__ void k_norm_finalize(const float* __restrict__ part, int nb, double s
     double n2 = sh[0];
     if (mode == 0) scal[0] = 0.0;
     if (n2 > 0.0) {
-      if (mode == 1) scal[0] += log(scale) + 0.5 * log(n2);
+      if (mode == 1) scal[0] += log(*scale_ptr) + 0.5 * log(n2);
       scal[1] = 1.0 / sqrt(n2);
     } else {
       scal[1] = 0.0;
@@ -142,20 +143,54 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void k_delta(const double* __restrict__ fro2a, double* __restrict__ scal, int ell) {
+  const double a = *fro2a, b = scal[kSfro2b];
+  const double delta = (a - b) / ((double)(6.0 / 41.0) * ell);
+  scal[kSdelta] = delta;
+  scal[kSscale] = delta > 0.0 ? 2.0 / delta : 0.0;
+  // Delta/2 at the resolution of the fp32 check: accept (64 * 2^-24 * ||A'||_F^2)
+  scal[kSsmall] = (delta / 2.0 <= 64.0 * 5.9604644775390625e-8 * a) ? 1.0 : 0.0;
+}
+
+__global__ void k_verdict(const double* __restrict__ fro2a, const double* __restrict__ scal,
+                          int verify, Verdict* __restrict__ out) {
+  Verdict v;
+  v.fro2a = *fro2a;
+  v.fro2b = scal[kSfro2b];
+  v.delta = scal[kSdelta];
+  v.small = scal[kSsmall] != 0.0;
+  v.zero = scal[kSzero] != 0.0;
+  v.logsum = v.small || v.zero ? -INFINITY : scal[kSlogsum];
+  v.ok = !verify || v.small || v.zero || v.logsum <= 0.0;
+  v.pad = 0;
+  *out = v;
+}
+
 }  // namespace
 
-double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
+void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s) {
+  k_delta<<<1, 1, 0, s>>>(fro2a, scal, ell);
+  SFD_LAUNCH_CHECK();
+}
+
+void launch_verdict(const double* fro2a, const double* scal, int verify, Verdict* out,
+                    cudaStream_t s) {
+  k_verdict<<<1, 1, 0, s>>>(fro2a, scal, verify, out);
+  SFD_LAUNCH_CHECK();
+}
+
+void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
   float* x = ws.vec0;   // d
   float* u = ws.vec1;   // m
   float* v = ws.vec2;   // d
   float* w = ws.wpart + kVsBlocks * kMaxEll;  // ell
   float* part = ws.wpart + kVsBlocks * kMaxEll + kMaxEll;  // kVsBlocks
-  double* scal = ws.scalars + 8;
+  double* scal = ws.scalars + kSlogsum;
   SFD_CUDA(cudaMemsetAsync(scal, 0, 4 * sizeof(double), s));
   launch_gauss_fill(x, a.d, 1, 1, a.seed, a.b, a.r, 2 /* tag of Alg. 6's x */, s);
   k_norm2_partial<<<kVsBlocks, 256, 0, s>>>(x, a.d, part);
   SFD_LAUNCH_CHECK();
-  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, 1.0, 0, scal);
+  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, nullptr, 0, scal);
   SFD_LAUNCH_CHECK();
   k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
   SFD_LAUNCH_CHECK();
@@ -168,17 +203,12 @@ double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
     spmv(*a.csc, u, v, ws.partial_rows, s);
     k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
     SFD_LAUNCH_CHECK();
-    k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale, 1, scal);
+    k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale_dev, 1, scal);
     SFD_LAUNCH_CHECK();
     std::swap(x, v);
     k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
     SFD_LAUNCH_CHECK();
   }
-  double h[3];
-  SFD_CUDA(cudaMemcpyAsync(h, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SFD_CUDA(cudaStreamSynchronize(s));
-  if (h[2] != 0.0) return -INFINITY;
-  return h[0];
 }
 
 }  // namespace sfd

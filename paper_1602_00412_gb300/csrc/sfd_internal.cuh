@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,23 @@
 #include "../../include/sfd.h"
 
 namespace sfd {
+
+// Schedules of the method (readings shared with the oracle):
+// q = ceil(c_q ln(m / eps) / eps), eps = 1/4 (Alg. 1 with the eps of Alg. 3)
+inline int q_for(const sfd_options& o, int m) {
+  if (o.q_override >= 0) return o.q_override;
+  double q = ceil(o.c_q * log((double)m / 0.25) / 0.25);
+  return q > 0 ? (int)q : 0;
+}
+// delta_{b,r} = delta (6/pi^2) / (b+1)^2 / 2^(r+1): the VS budget of buffer b, attempt r
+inline double delta_br(double delta, int64_t b, int r) {
+  return delta * (6.0 / (M_PI * M_PI)) / ((double)(b + 1) * (double)(b + 1)) / ldexp(1.0, r + 1);
+}
+// power steps p = ceil(log2(sqrt(2d/pi) / delta_i)) (Lemma 4.1)
+inline int vs_steps(int64_t d, double di) {
+  int p = (int)ceil(log2(sqrt(2.0 * (double)d / M_PI) / di));
+  return p > 1 ? p : 1;
+}
 
 // Dense blocks are row-major with the leading dimension padded to a multiple
 // of 8 floats, so every row starts on a 32-byte sector and float4 accesses
@@ -44,15 +62,18 @@ extern unsigned long long g_kernel_launches;
 
 // A CSR-like structure on the device (rows of A' for the CSR copy, columns
 // for the CSC copy) plus the work list that splits long segments.
+// The item and split counts stay on the device (no host round trip): kernels
+// are launched for the capacities and read the counts.
 struct SegWork {
   int2* items = nullptr;     // (segment, begin) ; end = min(begin + kSplit, ptr[seg+1])
   int* item_slot = nullptr;  // -1: item covers its whole segment, else partial slot
   int* split_seg = nullptr;  // segments cut into several items
   int* split_first = nullptr;// first item of each split segment
   int* split_count = nullptr;// items of each split segment
-  int* counters = nullptr;   // [0] items, [1] split segments, [2] slots
-  int n_items = 0, n_split = 0, n_slots = 0;  // host copies
-  int cap_items = 0;
+  int* counters = nullptr;   // offsets / scan scratch
+  const int* d_n_items = nullptr;  // device: number of items
+  const int* d_n_split = nullptr;  // device: number of split segments
+  int cap_items = 0, cap_split = 0;
 };
 
 struct Csr {
@@ -117,12 +138,19 @@ void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s
 // Philox4x64-10 Gaussian fill: out[i*ld + j] = normal #(i*cols + j) of (seed,b,r,tag).
 void launch_gauss_fill(float* out, int64_t rows, int cols, int ld, uint64_t seed, uint64_t b,
                        uint64_t r, uint64_t tag, cudaStream_t s);
-// Column map of a dense operand: columns [0,k0) at offset 0, [k0, k0+k1) at offset off1.
+// Column map of a dense operand made of two blocks: columns [0, k0) are
+// columns of X (leading dimension ldx), columns [k0, k0+k1) are columns of x1
+// (leading dimension ld1). Single blocks use k1 = 0.
 struct ColMap {
-  int k0, k1, off1;
+  int k0, k1;
+  const float* x1;
+  int ld1;
   __host__ __device__ int total() const { return k0 + k1; }
-  __host__ __device__ int col(int c) const { return c < k0 ? c : off1 + (c - k0); }
+  __device__ float at(const float* X, int ldx, int64_t g, int c) const {
+    return c < k0 ? X[g * ldx + c] : x1[g * ld1 + (c - k0)];
+  }
 };
+inline ColMap single_map(int k) { return ColMap{k, 0, nullptr, 0}; }
 // G = X^T X (n x n, n = map.total(), row-major ld n) over `rows` rows.
 void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
           cudaStream_t s);
@@ -134,9 +162,11 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
 // clamped.
 void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s);
 // Largest nwant eigenpairs of the symmetric n x n S: evals (descending),
-// evecs n x nwant row-major.
+// evecs n x nwant row-major. psd: S is a Gram matrix (positive semi-definite),
+// which allows the one-sided Jacobi path for n <= 128; otherwise (or for
+// larger n) tridiagonalisation + bisection + inverse iteration.
 void symeig(const float* S, int n, int nwant, float* evals, float* evecs, float* work,
-            cudaStream_t s);
+            cudaStream_t s, bool psd = false);
 size_t symeig_work_floats(int n, int nwant);
 // Shrink weights with threshold thr = ev[nkeep-1] (thr_zero: thr = 0, the
 // case of fewer than l rows): T[i][j] = evecs[i][j] * sqrt(max(0, 1 - thr/ev[j]))
@@ -158,11 +188,34 @@ struct VsArgs {
   const float* Bt;  // d x ld (B'^T)
   int ld, ell;
   int64_t d, m;
-  double scale;     // 2 / Delta
+  const double* scale_dev;  // device: 2 / Delta
   int p;
   uint64_t seed, b, r;
 };
-// Runs p power steps; returns log ||C^p x|| (host value).
-double verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s);
+// Enqueues p power steps; log ||C^p x|| lands in ws.scalars[kSlogsum],
+// ws.scalars[kSzero] = 1 if some C x_t vanished. No host synchronisation.
+void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s);
+
+// Device scalars of one SparseShrink attempt (ws.scalars[...]).
+enum : int {
+  kSfro2b = 0,   // ||B'||_F^2 (shrink_weights)
+  kSthr = 1,     // lambda_l^2
+  kSlogsum = 8,  // VerifySpectral log-sum
+  kSinvn = 9,    // its running inverse norm
+  kSzero = 10,   // some C x_t was zero
+  kSdelta = 16,  // Delta of Alg. 4
+  kSscale = 17,  // 2 / Delta
+  kSsmall = 18,  // Delta/2 at the fp32 resolution of ||A'||_F^2: accepted
+};
+// Verdict of one attempt, copied to pinned host memory.
+struct Verdict {
+  double fro2a, fro2b, delta, logsum;
+  int ok, small, zero, pad;
+};
+// Delta = (fro2a - fro2b) / (alpha l), scale = 2 / Delta, small flag.
+void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s);
+// Verdict from the device scalars (verify = 0: accepted).
+void launch_verdict(const double* fro2a, const double* scal, int verify, Verdict* out,
+                    cudaStream_t s);
 
 }  // namespace sfd

@@ -29,7 +29,8 @@ class sfd_options(ctypes.Structure):
                 ("q_override", ctypes.c_int32), ("retry_cap", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("q_mode", ctypes.c_int32),
                 ("strict", ctypes.c_int32), ("inject_vs_fail", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
+                ("slots", ctypes.c_int32)]
 
 
 class sfd_stats(ctypes.Structure):

@@ -46,7 +46,9 @@ def test_bssh_buffer_parity(lib, kind):
     assert info["q"] == q
     assert info["verified"] == 1 and rinfo["verified"]
     assert info["attempts"] == rinfo["attempts"]
-    assert abs(info["delta_shrink"] - rinfo["Delta"]) <= 1e-4 * abs(rinfo["Delta"])
+    # Delta = (||A'||^2 - ||B'||^2) / (alpha l) is a difference; its fp32 error is
+    # relative to the norms subtracted, not to the (possibly small) result
+    assert abs(info["delta_shrink"] - rinfo["Delta"]) * O.ALPHA * ell <= 1e-5 * info["fro2_a"]
     if kind == "gapped":
         assert rel <= TOL_BBT, rel
     else:
@@ -171,3 +173,12 @@ def test_invalid_input_leaves_context_usable(lib):
     s.append(rest.indptr, rest.indices, rest.values)
     assert np.array_equal(s.sketch().astype(np.float64), good)
     s.close()
+
+
+def test_pipeline_depth_does_not_change_the_sketch(lib):
+    # buffers run concurrently in slots, DenseShrink folds them in order:
+    # the sketch must be bit-identical for any number of slots
+    d, ell, seed = 2000, 50, 4
+    X = synth.c1_gapped(seed=seed, n=9000)
+    outs = [_run_gpu(lib, X, d, ell, seed, slots=s)[0] for s in (1, 2, 3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
