@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the cov-err evaluation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="0: FP32 throughout; 1: tensor-core (TF32) Gram and X R^-1 in the "
+                         "orthonormalisations of all but the last power iteration")
+    ap.add_argument("--slots", type=int, default=0, help="buffers in flight (0: library default)")
     return ap.parse_args()
 
 
@@ -230,7 +234,8 @@ def ours_arm(args, rank, world, local):
     ix_h = torch.from_numpy(X.indices).pin_memory().numpy()
     vv_h = torch.from_numpy(X.values).pin_memory().numpy()
     B_h = torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()
-    ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1)
+    ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1,
+                  precision=args.precision, slots=args.slots)
 
     def step_device():
         ctx.reset()
@@ -287,8 +292,10 @@ def ours_arm(args, rank, world, local):
     achieved = per_launch_bytes / per_launch_s / 1e9 if spmm_launches else None
     out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == 0 else "tf32+f32", "data": "synthetic",
            "config": {"workload": DESC, "rows": X.n, "d": d, "ell": ell, "nnz_per_rank": X.nnz,
+                      "precision": ["fp32", "mixed-tf32"][args.precision],
                       "buffers_per_step": st["buffers"], "attempts_per_step": st["attempts"],
                       "q_per_attempt": st["q_total"] / max(1, st["attempts"]),
                       "l2": "inputs larger than L2 (CSR stream %.0f MB per rank)" % (

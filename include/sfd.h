@@ -59,7 +59,10 @@ typedef struct sfd_options {
                            eps of Alg. 3); default 0.25, i.e. q = ceil(ln(4m)) */
   int32_t q_override;   /* >= 0: use this q for every buffer; -1 (default): the schedule above */
   int32_t retry_cap;    /* SparseShrink attempts per buffer before it is kept unverified (default 8) */
-  int32_t precision;    /* 0: plain fp32 (default); 1: mixed, tensor-core dense stages */
+  int32_t precision;    /* 0: plain fp32 (default); 1: mixed: for l <= 128 the orthonormalisations
+                           of every power iteration of Alg. 1 but the last form their Gram and
+                           X R^-1 on tcgen05 tensor cores (TF32 inputs, FP32 accumulation);
+                           every other stage stays FP32 */
   int32_t q_mode;       /* 0: fixed schedule (default); 1: learned predictor set by sfd_set_q_model */
   int32_t strict;       /* 1: a buffer left unverified makes sfd_append_rows return SFD_EVERIFY */
   int32_t inject_vs_fail; /* testing: force this many VerifySpectral verdicts to False (host-side) */
@@ -184,6 +187,19 @@ int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* col
 /* Orthonormalise the columns of X (rows x k, leading dimension ld, device) in
  * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */
 int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
+
+/* The two dense products of a CholeskyQR step (the GramSchmidt of Alg. 1):
+ * G = X^T X (k x k row-major, leading dimension k) over X (rows x k, leading
+ * dimension ldx), and Y = X T for T (n x kout row-major, leading dimension
+ * kout), X (rows x n, ldx), Y (rows x kout, ldy). All device memory; rows may
+ * be 0 (G = 0, Y untouched). precision 0: FP32 on the CUDA cores, sums in a
+ * fixed order (bit-reproducible); precision 1: tcgen05 tensor cores, inputs
+ * rounded to TF32 (10-bit mantissa), FP32 accumulation, for k, n, kout <= 128
+ * (larger returns SFD_EINVAL). Errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA,
+ * SFD_ETIMEOUT (a bounded tensor-core wait ran out; the outputs are not valid). */
+int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int32_t precision);
+int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const float* T, int32_t kout,
+                float* Y, int32_t ldy, int32_t precision);
 
 /* Symmetric eigendecomposition used by Alg. 3 / Alg. 5: the `nwant` largest
  * eigenvalues (descending, evals[nwant]) and their eigenvectors (evecs,

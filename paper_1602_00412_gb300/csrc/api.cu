@@ -135,6 +135,11 @@ int harvest_front(Ctx& C) {
   for (;;) {
     SFD_CUDA(cudaEventSynchronize(S.done));
     v = *S.verdict_host;
+    if (v.timeout) {  // a tensor-core wait expired: the attempt's result is not usable
+      C.st.attempts++;
+      status = SFD_ETIMEOUT;
+      break;
+    }
     C.st.attempts++;
     C.st.q_total += e.q;
     bool ok = v.ok != 0;
@@ -287,7 +292,8 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
   if (!ctx) return SFD_ENOMEM;
   Ctx& C = ctx->c;
   if (opt) C.opt = *opt; else sfd_options_init(&C.opt);
-  if (!(C.opt.delta > 0 && C.opt.delta < 1) || C.opt.c_q < 0 || C.opt.slots < 0) {
+  if (!(C.opt.delta > 0 && C.opt.delta < 1) || C.opt.c_q < 0 || C.opt.slots < 0 ||
+      (C.opt.precision != 0 && C.opt.precision != 1)) {
     delete ctx;
     return SFD_EINVAL;
   }
@@ -310,6 +316,7 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
       try {
         C.slots.emplace_back(new Slot(d, ell, d, cap_nnz, nullptr));
         C.slots.back()->profile = C.opt.profile != 0;
+        C.slots.back()->mixed = C.opt.precision == 1;
       } catch (const CudaError& e) {
         // fewer slots when memory is short; at least one is required
         if (e.err != cudaErrorMemoryAllocation || C.slots.empty()) throw;

@@ -153,11 +153,14 @@ void Slot::build(int m, int64_t nnz) {
   build_work(csc, stream);
 }
 
-void Slot::orth_pass(const float* X, int64_t rows, float* Xout) {
+void Slot::orth_pass(const float* X, int64_t rows, float* Xout, bool tc) {
   const ColMap map = single_map(ell);
-  gram(X, ld, map, rows, ws.small_a, ws, stream);
+  tc = tc && tc_supported(ell, ell);
+  if (tc) gram_tc(X, ld, map, rows, ws.small_a, ws, stream);
+  else gram(X, ld, map, rows, ws.small_a, ws, stream);
   chol_inv(ws.small_a, ell, ws.small_b, ws.eig_work, ws.flags, stream);
-  gemm_ts(X, ld, map, rows, ws.small_b, ell, Xout, ld, stream);
+  if (tc) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream);
+  else gemm_ts(X, ld, map, rows, ws.small_b, ell, Xout, ld, stream);
 }
 
 void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in) {
@@ -198,18 +201,23 @@ void Slot::collect_profile() {
 void Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify) {
   // Alg. 1: G ~ N(0,1)^{d x l}; Y = orth(A' G); q x { W = orth(A'^T Y); Y = orth(A' W) }
   launch_gauss_fill(W, d, ell, ld, seed, b, r, 1, stream);
+  // mixed precision: the orthonormalisations of every power iteration but the
+  // last run on tensor cores; the last iteration and the second CholeskyQR
+  // pass on Z stay FP32, so the TF32 perturbation of the subspace is damped by
+  // one more FP32 iteration and Z is orthonormal to FP32 accuracy
   spmm_timed(csr, W, Y, d);
-  orth_pass(Y, m, Y2);
+  orth_pass(Y, m, Y2, mixed && q > 0);
   std::swap(Y, Y2);
   for (int t = 0; t < q; ++t) {
+    const bool tc = mixed && t + 1 < q;
     spmm_timed(csc, Y, W, m);
-    orth_pass(W, d, W2);
+    orth_pass(W, d, W2, tc);
     std::swap(W, W2);
     spmm_timed(csr, W, Y, d);
-    orth_pass(Y, m, Y2);
+    orth_pass(Y, m, Y2, tc);
     std::swap(Y, Y2);
   }
-  orth_pass(Y, m, Y2);  // second CholeskyQR pass on Z
+  orth_pass(Y, m, Y2, false);  // second CholeskyQR pass on Z
   std::swap(Y, Y2);
   // Alg. 3: P^T = A'^T Z, svd(P, l) through P P^T, B'^T = P^T H diag(s)
   spmm_timed(csc, Y, W, m);
@@ -225,7 +233,7 @@ void Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, 
     VsArgs a{&csr, &csc, Bpt, ld, ell, d, m, ws.scalars + kSscale, p, seed, b, r};
     verify_spectral(a, ws, stream);
   }
-  launch_verdict(fro2, ws.scalars, verify, verdict_dev, stream);
+  launch_verdict(fro2, ws.scalars, ws.flags, verify, verdict_dev, stream);
   SFD_CUDA(cudaMemcpyAsync(verdict_host, verdict_dev, sizeof(Verdict), cudaMemcpyDeviceToHost,
                            stream));
   SFD_CUDA(cudaEventRecord(done, stream));

@@ -61,6 +61,9 @@ struct Slot {
   Verdict* verdict_dev = nullptr;
   Verdict* verdict_host = nullptr;  // pinned
   int* ptr_host = nullptr;          // pinned staging of the local row pointer
+  // precision 1: the orthonormalisations inside the power iterations run their
+  // Gram and X R^-1 on tensor cores (TF32 inputs, FP32 accumulate)
+  bool mixed = false;
   // profiling of the sparse products
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -85,7 +88,7 @@ struct Slot {
 
  private:
   void cleanup();
-  void orth_pass(const float* X, int64_t rows, float* Xout);
+  void orth_pass(const float* X, int64_t rows, float* Xout, bool tc);
   void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in);
 };
 

@@ -538,6 +538,12 @@ void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace
   SFD_LAUNCH_CHECK();
 }
 
+void gram_reduce_tiles(const float* partial, int nchunks, int n, float* G, cudaStream_t s) {
+  int64_t ne = (int64_t)n * n;
+  k_gram_reduce<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(partial, nchunks, 1, 1, n, G);
+  SFD_LAUNCH_CHECK();
+}
+
 void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout, float* Y,
              int ldy, cudaStream_t s) {
   if (rows <= 0 || kout <= 0) return;

@@ -1,0 +1,368 @@
+// Tensor-core (tcgen05, kind::tf32) forms of the two dense products of
+// CholeskyQR inside SimultaneousIteration (Alg. 1): the Gram X^T X and the
+// tall-skinny product X T, for blocks of at most 128 columns.
+//
+// Operands are staged by the CTA's threads into shared memory in the K-major
+// canonical layout without swizzle: core matrices of 8 rows x 16 bytes
+// (4 tf32 along K); element (r, k) of an R x K tile sits at byte
+//   ((r / 8) * (K / 4) + k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4,
+// so the descriptor's leading byte offset (next core along K) is 128 and its
+// stride byte offset (next 8 rows) is K * 32. One thread issues the MMAs
+// (M = 128, K = 8 each), the accumulator lives in tensor memory, and the
+// epilogue reads it back with tcgen05.ld. Every mbarrier wait is bounded: on
+// expiry the kernel sets flags[2], waits once more (bounded), frees its tensor
+// memory and returns.
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version bits 46-48 = 0b001
+  return d;
+}
+
+// Instruction descriptor: f32 accumulate, tf32 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ int core_off(int r, int k, int K) {  // in floats
+  return (((r >> 3) * (K >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4) >> 2;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(mbar)));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity));
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(cols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::);
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
+
+// ------------------------------------------------------------------ Gram
+// partial[chunk] (128 x 128 row-major; only the leading n x n block is
+// written) = X[rows of chunk, 0:n]^T X[rows of chunk, 0:n]. Rows are staged
+// 32 at a time (K = 32: four MMAs) into two buffers; a buffer is refilled once
+// the MMAs that read it have completed. Staging: a thread gathers one column
+// m of four consecutive rows (coalesced across the warp) and stores them as
+// one 16-byte row of a core matrix, so eight lanes fill one core (conflict free).
+constexpr int kGK = 32;             // rows per stage
+constexpr int kGTile = 128 * kGK;   // floats per stage
+constexpr int kGramSmem = 48 * 1024;  // 2 stages (32 KB) padded: at most 4 CTAs (512 TMEM columns) per SM
+constexpr int kGramChunks = 152;
+
+__global__ void __launch_bounds__(kTcThreads)
+    k_tc_gram(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
+              int64_t rows_per_chunk, float* __restrict__ partial, int* __restrict__ flags) {
+  extern __shared__ __align__(1024) float smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = map.total();
+  if (warp == 0) tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, 128);
+  const int64_t r_beg = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  uint32_t phase[2] = {0u, 0u};
+  int used[2] = {0, 0};
+  bool ok = true;
+  int stage = 0;
+  for (int64_t r0 = r_beg; r0 < r_end; r0 += kGK, ++stage) {
+    const int b = stage & 1;
+    float* tile = smem + b * kGTile;
+    if (used[b]) {  // the MMAs issued on this buffer two stages ago must be done
+      const bool w = mbar_wait(&mbar[b], phase[b]);
+      if (!__syncthreads_and(w)) { ok = false; break; }
+      phase[b] ^= 1u;
+    }
+#pragma unroll 2
+    for (int it = 0; it < (kGK / 4) * 128 / kTcThreads; ++it) {
+      const int i = tid + it * kTcThreads;
+      const int m = i & 127, kc = i >> 7;  // column of X, group of 4 rows
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t g = r0 + kc * 4 + j;
+        v[j] = (g < r_end && m < n) ? map.at(X, ldx, g, m) : 0.f;
+      }
+      *reinterpret_cast<float4*>(&tile[core_off(m, kc * 4, kGK)]) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::);
+      const uint32_t base = smem_u32(tile);
+#pragma unroll
+      for (int kk = 0; kk < kGK / 8; ++kk) {
+        const uint64_t da = smem_desc(base + kk * 256, 128, kGK * 32);
+        mma_tf32(tmem, da, da, idesc, (stage > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&mbar[b]);
+    }
+    used[b] = 1;
+  }
+  if (ok && stage > 0) {  // the last commit tracks every MMA issued before it
+    const int b = (stage - 1) & 1;
+    ok = __syncthreads_and(mbar_wait(&mbar[b], phase[b]));
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&flags[2], 1);
+    for (int b = 0; b < 2; ++b)  // bounded: let MMAs in flight finish before freeing
+      if (used[b]) mbar_wait(&mbar[b], phase[b]);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  __syncthreads();
+  float* out = partial + (int64_t)blockIdx.x * (128 * 128);
+  const int m = warp * 32 + lane;
+  const bool have = ok && stage > 0;
+  for (int c0 = 0; c0 < n; c0 += 16) {
+    float v[16];
+    if (have) {
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    }
+    if (m < n) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(&out[m * 128 + c0 + j]) =
+            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 128);
+}
+
+// ----------------------------------------------------------------- X * T
+// Y[rows, 0:kout] = X[rows, 0:n] T (T: n x kout, row-major). T^T (Np x Kp,
+// n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA; each 128-row
+// tile of X is staged (eight lanes fill one core matrix with 16-byte rows),
+// multiplied with Kp / 8 MMAs and written back from tensor memory, one row per
+// thread.
+__global__ void __launch_bounds__(kTcThreads)
+    k_tc_gemm(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
+              const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
+              int ldy, int* __restrict__ flags) {
+  extern __shared__ __align__(1024) float smem[];
+  float* Bs = smem;            // Np x Kp
+  float* As = smem + Np * Kp;  // 128 x Kp
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = map.total();
+  const int kc_n = Kp >> 2;  // 16-byte chunks along K
+  if (warp == 0) tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  for (int i = tid; i < Np * kc_n; i += kTcThreads) {  // B(j, k) = T[k][j]
+    const int j = i % Np, kc = i / Np;
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = kc * 4 + t;
+      v[t] = (k < n && j < kout) ? T[(int64_t)k * kout + j] : 0.f;
+    }
+    *reinterpret_cast<float4*>(&Bs[core_off(j, kc * 4, Kp)]) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, Np);
+  const int64_t ntiles = (rows + 127) / 128;
+  const bool vec = map.k1 == 0 && (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
+  const bool vec_out = (ldy & 3) == 0 && ((uintptr_t)Y & 15) == 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row0 = t * 128;
+    for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
+      const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
+      const int64_t g = row0 + r;
+      const int k = kc * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g < rows) {
+        if (vec && k + 4 <= n) {
+          v = *reinterpret_cast<const float4*>(&X[g * ldx + k]);
+        } else {
+          v.x = k + 0 < n ? map.at(X, ldx, g, k + 0) : 0.f;
+          v.y = k + 1 < n ? map.at(X, ldx, g, k + 1) : 0.f;
+          v.z = k + 2 < n ? map.at(X, ldx, g, k + 2) : 0.f;
+          v.w = k + 3 < n ? map.at(X, ldx, g, k + 3) : 0.f;
+        }
+      }
+      *reinterpret_cast<float4*>(&As[core_off(r, k, Kp)]) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::);
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int kk = 0; kk < Kp / 8; ++kk) {
+        const uint64_t da = smem_desc(a0 + kk * 256, 128, Kp * 32);
+        const uint64_t db = smem_desc(b0 + kk * 256, 128, Kp * 32);
+        mma_tf32(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
+      }
+      mma_commit(&mbar);
+    }
+    if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::);
+    const int r = warp * 32 + lane;
+    const int64_t g = row0 + r;
+    for (int c0 = 0; c0 < Np; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (g < rows) {
+        float* y = Y + g * ldy + c0;
+        if (vec_out && c0 + 16 <= kout) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(&y[j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < kout) y[j] = v[j];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::);
+    __syncthreads();  // tensor memory and the A tile are free again
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&flags[2], 1);
+    mbar_wait(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 128);
+}
+
+}  // namespace
+
+bool tc_supported(int n, int kout) { return n >= 1 && n <= 128 && kout >= 1 && kout <= 128; }
+
+void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
+             cudaStream_t s) {
+  const int n = map.total();
+  if (!tc_supported(n, n)) throw CudaError{cudaErrorInvalidValue, "gram_tc: n > 128"};
+  static std::atomic<unsigned> attr{0};
+  int dev = 0;
+  SFD_CUDA(cudaGetDevice(&dev));
+  if (dev < 32 && !(attr.load() & (1u << dev))) {
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kGramSmem));
+    attr.fetch_or(1u << dev);
+  }
+  int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kGK - 1) / kGK, kGramChunks));
+  int64_t rpc = (rows + nchunks - 1) / nchunks;
+  rpc = ((rpc + kGK - 1) / kGK) * kGK;
+  nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
+  if (rows > 0) {
+    k_tc_gram<<<nchunks, kTcThreads, kGramSmem, s>>>(X, ldx, map, rows, rpc, ws.gram_partial,
+                                                     ws.flags);
+    SFD_LAUNCH_CHECK();
+  } else {
+    nchunks = 0;
+  }
+  gram_reduce_tiles(ws.gram_partial, nchunks, n, G, s);
+}
+
+void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
+                float* Y, int ldy, Workspace& ws, cudaStream_t s) {
+  if (rows <= 0 || kout <= 0) return;
+  const int n = map.total();
+  if (!tc_supported(n, kout)) throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: n or kout > 128"};
+  const int Kp = (n + 7) & ~7;
+  const int Np = (kout + 15) & ~15;
+  static std::atomic<unsigned> attr{0};
+  int dev = 0;
+  SFD_CUDA(cudaGetDevice(&dev));
+  if (dev < 32 && !(attr.load() & (1u << dev))) {
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * 128 * 128 * (int)sizeof(float)));
+    attr.fetch_or(1u << dev);
+  }
+  const size_t bytes = (size_t)(Np * Kp + 128 * Kp) * sizeof(float);
+  const int64_t ntiles = (rows + 127) / 128;
+  const int grid = (int)std::min<int64_t>(ntiles, 2 * 152);
+  k_tc_gemm<<<grid, kTcThreads, bytes, s>>>(X, ldx, map, rows, T, kout, Kp, Np, Y, ldy, ws.flags);
+  SFD_LAUNCH_CHECK();
+}
+
+}  // namespace sfd

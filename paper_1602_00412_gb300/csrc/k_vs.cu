@@ -153,7 +153,7 @@ __global__ void k_delta(const double* __restrict__ fro2a, double* __restrict__ s
 }
 
 __global__ void k_verdict(const double* __restrict__ fro2a, const double* __restrict__ scal,
-                          int verify, Verdict* __restrict__ out) {
+                          const int* __restrict__ flags, int verify, Verdict* __restrict__ out) {
   Verdict v;
   v.fro2a = *fro2a;
   v.fro2b = scal[kSfro2b];
@@ -162,7 +162,7 @@ __global__ void k_verdict(const double* __restrict__ fro2a, const double* __rest
   v.zero = scal[kSzero] != 0.0;
   v.logsum = v.small || v.zero ? -INFINITY : scal[kSlogsum];
   v.ok = !verify || v.small || v.zero || v.logsum <= 0.0;
-  v.pad = 0;
+  v.timeout = flags[2];
   *out = v;
 }
 
@@ -173,9 +173,9 @@ void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s) {
   SFD_LAUNCH_CHECK();
 }
 
-void launch_verdict(const double* fro2a, const double* scal, int verify, Verdict* out,
-                    cudaStream_t s) {
-  k_verdict<<<1, 1, 0, s>>>(fro2a, scal, verify, out);
+void launch_verdict(const double* fro2a, const double* scal, const int* flags, int verify,
+                    Verdict* out, cudaStream_t s) {
+  k_verdict<<<1, 1, 0, s>>>(fro2a, scal, flags, verify, out);
   SFD_LAUNCH_CHECK();
 }
 

@@ -46,6 +46,29 @@ bool load_slot(Slot& S, int64_t m, int64_t nnz, const int32_t* rowptr, const int
   return bad == 0;
 }
 
+// Shared body of the two dense products: scratch, stream, timeout flag.
+template <typename F>
+int run_dense(F&& f) {
+  DevArena A;
+  cudaStream_t s = nullptr;
+  try {
+    SFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    Workspace ws;
+    alloc_dense_scratch(A, ws);
+    f(ws, s);
+    int flags[4] = {0, 0, 0, 0};
+    SFD_CUDA(cudaMemcpyAsync(flags, ws.flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    SFD_CUDA(cudaStreamSynchronize(s));
+    A.release();
+    cudaStreamDestroy(s);
+    return flags[2] ? SFD_ETIMEOUT : SFD_OK;
+  } catch (const CudaError& e) {
+    A.release();
+    if (s) cudaStreamDestroy(s);
+    return code_of(e);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -165,6 +188,27 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
     if (s) cudaStreamDestroy(s);
     return code_of(e);
   }
+}
+
+int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int32_t precision) {
+  if (rows < 0 || k < 1 || k > kMaxEll || ldx < k || !G || (rows > 0 && !X)) return SFD_EINVAL;
+  if (precision != 0 && !(precision == 1 && tc_supported(k, k))) return SFD_EINVAL;
+  return run_dense([&](Workspace& ws, cudaStream_t s) {
+    if (precision == 1) gram_tc(X, ldx, single_map(k), rows, G, ws, s);
+    else gram(X, ldx, single_map(k), rows, G, ws, s);
+  });
+}
+
+int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const float* T, int32_t kout,
+                float* Y, int32_t ldy, int32_t precision) {
+  if (rows < 0 || n < 1 || n > kMaxEll || kout < 1 || kout > kMaxEll || ldx < n || ldy < kout ||
+      !T || (rows > 0 && (!X || !Y)))
+    return SFD_EINVAL;
+  if (precision != 0 && !(precision == 1 && tc_supported(n, kout))) return SFD_EINVAL;
+  return run_dense([&](Workspace& ws, cudaStream_t s) {
+    if (precision == 1) gemm_ts_tc(X, ldx, single_map(n), rows, T, kout, Y, ldy, ws, s);
+    else gemm_ts(X, ldx, single_map(n), rows, T, kout, Y, ldy, s);
+  });
 }
 
 int sfd_symeig(int32_t n, const float* S, int32_t nwant, float* evals, float* evecs) {

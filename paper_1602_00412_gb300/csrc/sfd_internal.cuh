@@ -157,6 +157,15 @@ void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace
 // Y[:, 0:kout] = X[:, map] * T (T: n x kout row-major, ld kout).
 void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout, float* Y,
              int ldy, cudaStream_t s);
+// G = X^T X reduced from 128 x 128 partial tiles (one per chunk of rows).
+void gram_reduce_tiles(const float* partial, int nchunks, int n, float* G, cudaStream_t s);
+// Tensor-core (tcgen05 kind::tf32, FP32 accumulate) forms of gram and
+// gemm_ts for n, kout <= 128. A wait that expires sets flags[2].
+bool tc_supported(int n, int kout);
+void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
+             cudaStream_t s);
+void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
+                float* Y, int ldy, Workspace& ws, cudaStream_t s);
 // Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
 // row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
 // clamped.
@@ -210,12 +219,13 @@ enum : int {
 // Verdict of one attempt, copied to pinned host memory.
 struct Verdict {
   double fro2a, fro2b, delta, logsum;
-  int ok, small, zero, pad;
+  int ok, small, zero, timeout;  // timeout: a bounded device wait expired (flags[2])
 };
 // Delta = (fro2a - fro2b) / (alpha l), scale = 2 / Delta, small flag.
 void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s);
 // Verdict from the device scalars (verify = 0: accepted).
-void launch_verdict(const double* fro2a, const double* scal, int verify, Verdict* out,
+void launch_verdict(const double* fro2a, const double* scal, const int* flags, int verify,
+                    Verdict* out,
                     cudaStream_t s);
 
 }  // namespace sfd

@@ -52,7 +52,7 @@ class sfd_shrink_info(ctypes.Structure):
 EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "sfd_merge",
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
            "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig",
-           "sfd_symeig_noalloc"]
+           "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts"]
 
 _lib = None
 
@@ -89,6 +89,8 @@ def load(path=None):
     L.sfd_orthonormalize.argtypes = [i64, i32, vp, i32]
     L.sfd_symeig.argtypes = [i32, vp, i32, vp, vp]
     L.sfd_symeig_noalloc.argtypes = [i32, vp, i32, vp, vp]
+    L.sfd_gram.argtypes = [i64, i32, vp, i32, vp, i32]
+    L.sfd_gemm_ts.argtypes = [i64, i32, vp, i32, vp, i32, vp, i32, i32]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error"):
@@ -211,6 +213,17 @@ def sfd_csr_spmm(m, d, rowptr, colidx, vals, k, X, ldx, Y, ldy, transpose):
 
 def sfd_orthonormalize(rows, k, X, ld):
     _check(load().sfd_orthonormalize(rows, k, ctypes.c_void_p(X.data_ptr()), ld))
+
+
+def sfd_gram(rows, k, X, ldx, G, precision=0):
+    _check(load().sfd_gram(rows, k, ctypes.c_void_p(X.data_ptr()), ldx,
+                           ctypes.c_void_p(G.data_ptr()), int(precision)))
+
+
+def sfd_gemm_ts(rows, n, X, ldx, T, kout, Y, ldy, precision=0):
+    _check(load().sfd_gemm_ts(rows, n, ctypes.c_void_p(X.data_ptr()), ldx,
+                              ctypes.c_void_p(T.data_ptr()), kout, ctypes.c_void_p(Y.data_ptr()),
+                              ldy, int(precision)))
 
 
 def sfd_symeig(n, S, nwant, evals, evecs):
