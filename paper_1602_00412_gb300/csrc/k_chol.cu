@@ -1,0 +1,221 @@
+// Cholesky factor and its inverse for CholeskyQR (the GramSchmidt step of
+// Alg. 1): G + shift I = L L^T and Rinv = L^-T, for k <= 128, one CTA.
+//
+// Blocked right-looking factorisation with 16-wide panels. For each panel:
+//   1. one warp factors the 16 x 16 diagonal block in registers (lane i holds
+//      row i; L[t][j] is broadcast with shuffles) and inverts it by forward
+//      substitution (lane c solves column c);
+//   2. the panel below is L21 = A21 L11^-T (a 16-term product per entry);
+//   3. the trailing lower triangle is updated, A22 -= L21 L21^T, in 4 x 4
+//      register tiles.
+// Then the off-diagonal blocks of L^-1 follow block diagonal by block
+// diagonal: X_ij = -X_ii sum_{t=j}^{i-1} L_it X_tj. That is 3 barriers per
+// panel and 2 per block diagonal, instead of one per column.
+#include <atomic>
+
+#include "sfd_internal.cuh"
+
+namespace sfd {
+namespace {
+
+constexpr int kCB = 16;         // panel width
+constexpr int kCThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+__global__ void __launch_bounds__(kCThreads)
+    k_chol_inv_blk(const float* __restrict__ G, int k, float* __restrict__ Rinv,
+                   int* __restrict__ flags) {
+  extern __shared__ float sm[];
+  const int KP = (k + kCB - 1) / kCB * kCB;  // padded with the identity
+  const int LD = KP + 1;
+  const int NB = KP / kCB;
+  float* A = sm;             // KP x LD, lower triangle becomes L
+  float* Li = A + KP * LD;   // KP x LD, lower triangle becomes L^-1
+  float* S = Li + KP * LD;   // NB x 256 scratch
+  __shared__ float red[kCThreads / 32];
+  __shared__ float shift_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // G's entries arrive by cp.async (all in flight at once); padding is the identity
+  for (int e = tid; e < KP * KP; e += kCThreads) {
+    const int i = e / KP, j = e - (e / KP) * KP;
+    if (i < k && j < k) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&A[i * LD + j]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + (int64_t)i * k + j));
+    } else {
+      A[i * LD + j] = (i == j) ? 1.f : 0.f;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::);
+  asm volatile("cp.async.wait_group 0;" ::);
+  __syncthreads();
+  float tr = 0.f;
+  for (int i = tid; i < k; i += kCThreads) tr += A[i * LD + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(kFull, tr, o);
+  if (lane == 0) red[warp] = tr;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kCThreads / 32; ++w) t += red[w];
+    shift_sh = t > 0.f ? ldexpf(t / (float)k, -20) : 1e-30f;
+  }
+  __syncthreads();
+  const float shift = shift_sh;
+  for (int i = tid; i < k; i += kCThreads) A[i * LD + i] += shift;
+  __syncthreads();
+
+  for (int p = 0; p < NB; ++p) {
+    const int j0 = p * kCB;
+    // ---- 1. diagonal block: factor and invert in registers (warp 0)
+    if (warp == 0) {
+      const int i = lane & 15;  // lanes 16..31 repeat lanes 0..15
+      float d[kCB];
+#pragma unroll
+      for (int t = 0; t < kCB; ++t) d[t] = A[(j0 + i) * LD + j0 + t];
+      int clamped = 0;
+#pragma unroll
+      for (int j = 0; j < kCB; ++j) {
+        float piv = __shfl_sync(kFull, d[j], j);
+        clamped += !(piv > 0.f);
+        piv = piv > 0.f ? piv : shift;
+        const float ljj = sqrtf(piv), inv = 1.f / ljj;
+        const float lij = i > j ? d[j] * inv : (i == j ? ljj : 0.f);
+        d[j] = lij;
+#pragma unroll
+        for (int t = 0; t < kCB; ++t) {
+          if (t > j) {
+            const float ltj = __shfl_sync(kFull, lij, t);
+            if (t <= i) d[t] = fmaf(-lij, ltj, d[t]);
+          }
+        }
+      }
+      if (lane == 0 && clamped) atomicAdd(&flags[1], clamped);
+      // column c = i of the inverse of the block
+      float x[kCB];
+#pragma unroll
+      for (int r = 0; r < kCB; ++r) {
+        float s = r == i ? 1.f : 0.f;
+#pragma unroll
+        for (int t = 0; t < r; ++t) s = fmaf(-__shfl_sync(kFull, d[t], r), x[t], s);
+        const float lrr = __shfl_sync(kFull, d[r], r);
+        x[r] = r >= i ? s / lrr : 0.f;
+      }
+      if (lane < kCB) {
+#pragma unroll
+        for (int t = 0; t < kCB; ++t) {
+          if (t <= i) A[(j0 + i) * LD + j0 + t] = d[t];
+          Li[(j0 + t) * LD + j0 + i] = x[t];  // column i; zero above the diagonal
+        }
+      }
+    }
+    __syncthreads();
+    const int below = KP - j0 - kCB;
+    if (below == 0) break;
+    // ---- 2. panel below: L21[r][c] = sum_{t<=c} A21[r][t] Linv11[c][t]
+    //         (one thread per row: it reads the whole row before writing it)
+    if (tid < below) {
+      const int r = j0 + kCB + tid;
+      const float* X = Li + j0 * LD + j0;
+      float a[kCB];
+#pragma unroll
+      for (int t = 0; t < kCB; ++t) a[t] = A[r * LD + j0 + t];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t <= c; ++t) s = fmaf(a[t], X[c * LD + t], s);
+        A[r * LD + j0 + c] = s;
+      }
+    }
+    __syncthreads();
+    // ---- 3. trailing update of the lower triangle in 4 x 4 tiles
+    {
+      const int nb4 = below >> 2;
+      const int ntile = nb4 * (nb4 + 1) / 2;
+      const int base = j0 + kCB;
+      for (int e = tid; e < ntile; e += kCThreads) {
+        int bi = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while (bi * (bi + 1) / 2 > e) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
+        const int bj = e - bi * (bi + 1) / 2;
+        const int r0 = base + bi * 4, c0 = base + bj * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+        for (int t = 0; t < kCB; ++t) {
+          float xr[4], yc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            xr[u] = A[(r0 + u) * LD + j0 + t];
+            yc[u] = A[(c0 + u) * LD + j0 + t];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xr[u], yc[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (c0 + v <= r0 + u) A[(r0 + u) * LD + c0 + v] -= acc[u][v];
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- off-diagonal blocks of L^-1, one block diagonal at a time
+  for (int dl = 1; dl < NB; ++dl) {
+    const int nout = (NB - dl) * kCB * kCB;
+    for (int e = tid; e < nout; e += kCThreads) {
+      const int jb = e >> 8, rr = (e >> 4) & 15, cc = e & 15;
+      const int ib = jb + dl;
+      const int row = ib * kCB + rr, col = jb * kCB + cc;
+      float s = 0.f;
+      for (int t = col; t < ib * kCB; ++t) s = fmaf(A[row * LD + t], Li[t * LD + col], s);
+      S[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < nout; e += kCThreads) {
+      const int jb = e >> 8, rr = (e >> 4) & 15, cc = e & 15;
+      const int ib = jb + dl;
+      const int row = ib * kCB + rr, col = jb * kCB + cc;
+      float s = 0.f;
+      for (int u = 0; u <= rr; ++u)
+        s = fmaf(Li[row * LD + ib * kCB + u], S[(jb << 8) + (u << 4) + cc], s);
+      Li[row * LD + col] = -s;
+    }
+    __syncthreads();
+  }
+  // Rinv = (L^-1)^T, upper triangular
+  for (int e = tid; e < k * k; e += kCThreads) {
+    const int c = e / k, i = e - (e / k) * k;
+    Rinv[e] = c <= i ? Li[i * LD + c] : 0.f;
+  }
+}
+
+}  // namespace
+
+size_t chol_blk_smem_bytes(int k) {
+  const int KP = (k + kCB - 1) / kCB * kCB;
+  return ((size_t)2 * KP * (KP + 1) + (size_t)(KP / kCB) * kCB * kCB) * sizeof(float);
+}
+
+void chol_inv_blk(const float* G, int k, float* Rinv, int* flags, cudaStream_t s) {
+  static std::atomic<unsigned> attr{0};
+  int dev = 0;
+  SFD_CUDA(cudaGetDevice(&dev));
+  if (dev < 32 && !(attr.load() & (1u << dev))) {
+    SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)chol_blk_smem_bytes(128)));
+    attr.fetch_or(1u << dev);
+  }
+  k_chol_inv_blk<<<1, kCThreads, chol_blk_smem_bytes(k), s>>>(G, k, Rinv, flags);
+  SFD_LAUNCH_CHECK();
+}
+
+}  // namespace sfd

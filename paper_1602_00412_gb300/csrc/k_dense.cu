@@ -136,29 +136,45 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-__global__ void k_gram_reduce(const float* __restrict__ partial, int nchunks, int npairs,
-                              int ntiles, int n, float* __restrict__ G) {
-  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n * n) return;
-  int i = (int)(e / n), j = (int)(e % n);
-  int a = i, c = j;
-  if (a / kT > c / kT) { int t = a; a = c; c = t; }   // use the upper tile (ti <= tj)
-  const int ti = a / kT, tj = c / kT;
-  const int tp = ti * ntiles - ti * (ti - 1) / 2 + (tj - ti);
-  const int off = (a % kT) * kT + (c % kT);
-  const float* p = partial + (int64_t)tp * (kT * kT) + off;
-  const int64_t stride = (int64_t)npairs * (kT * kT);
-  // four interleaved accumulators, combined in a fixed order (deterministic)
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int ch = 0;
-  for (; ch + 4 <= nchunks; ch += 4) {
-    s0 += p[(ch + 0) * stride];
-    s1 += p[(ch + 1) * stride];
-    s2 += p[(ch + 2) * stride];
-    s3 += p[(ch + 3) * stride];
+// G[e] = sum over chunks of the partial tiles. A block takes 32 consecutive
+// output elements; its 8 warps each sum every 8th chunk (coalesced 128-byte
+// reads per chunk), and the 8 warp sums are added in a fixed order, so the
+// result does not depend on scheduling.
+constexpr int kRedGroups = 8;
+
+__global__ void __launch_bounds__(32 * kRedGroups)
+    k_gram_reduce(const float* __restrict__ partial, int nchunks, int npairs, int ntiles, int n,
+                  float* __restrict__ G) {
+  __shared__ float sums[kRedGroups][33];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const bool live = e < (int64_t)n * n;
+  float acc = 0.f;
+  if (live) {
+    int a = (int)(e / n), c = (int)(e % n);
+    if (a / kT > c / kT) { int t = a; a = c; c = t; }   // use the upper tile (ti <= tj)
+    const int ti = a / kT, tj = c / kT;
+    const int tp = ti * ntiles - ti * (ti - 1) / 2 + (tj - ti);
+    const int off = (a % kT) * kT + (c % kT);
+    const float* p = partial + (int64_t)tp * (kT * kT) + off;
+    const int64_t stride = (int64_t)npairs * (kT * kT);
+    float s0 = 0.f, s1 = 0.f;
+    int ch = grp;
+    for (; ch + kRedGroups < nchunks; ch += 2 * kRedGroups) {
+      s0 += p[ch * stride];
+      s1 += p[(ch + kRedGroups) * stride];
+    }
+    if (ch < nchunks) s0 += p[ch * stride];
+    acc = s0 + s1;
   }
-  for (; ch < nchunks; ++ch) s0 += p[ch * stride];
-  G[e] = (s0 + s1) + (s2 + s3);
+  sums[grp][lane] = acc;
+  __syncthreads();
+  if (grp == 0 && live) {
+    float t = 0.f;
+#pragma unroll
+    for (int g = 0; g < kRedGroups; ++g) t += sums[g][lane];
+    G[e] = t;
+  }
 }
 
 // ---------------------------------------------------------------- X * T
@@ -301,157 +317,6 @@ __global__ void __launch_bounds__(kCholThreads)
   }
 }
 
-// Register-tiled Cholesky + inverse for k <= 128: 16 x 16 threads, element
-// (i, t) lives in thread (i % 16, t % 16), register (i / 16, t / 16) (cyclic,
-// so every thread keeps work as the factorisation shrinks). One barrier per
-// step: step j publishes the raw column j (and its pivot) into one of two
-// shared buffers; every thread scales on the fly, so the next step can fill
-// the other buffer while slow threads still read this one.
-//  - Cholesky: A[i][t] -= c_i c_t / c_j for j < t <= i (c = raw column j),
-//    L[i][j] = c_i / sqrt(c_j) kept in shared memory for the inverse.
-//  - Inverse: forward substitution L X = I on all columns at once with the
-//    right-hand sides in registers; Rinv = X^T.
-template <int TL>
-__device__ __forceinline__ float sel_reg(const float (&a)[TL][TL], int p, int q) {
-  float v = 0.f;
-#pragma unroll
-  for (int pp = 0; pp < TL; ++pp)
-#pragma unroll
-    for (int qq = 0; qq < TL; ++qq)
-      if (pp == p && qq == q) v = a[pp][qq];
-  return v;
-}
-
-template <int TL>
-__global__ void __launch_bounds__(256)
-    k_chol_inv_reg(const float* __restrict__ G, int k, float* __restrict__ Rinv,
-                   int* __restrict__ flags) {
-  extern __shared__ float Lsm[];        // L[i][j] at Lsm[j * LS + i] (column j contiguous)
-  __shared__ float buf[2][129];         // raw column / row, slot 128 holds the pivot
-  __shared__ float red[33];
-  const int tid = threadIdx.x;
-  const int ty = tid >> 4, tx = tid & 15;
-  const int LS = k + 1;
-  float a[TL][TL];
-  float tr = 0.f;
-#pragma unroll
-  for (int p = 0; p < TL; ++p)
-#pragma unroll
-    for (int q = 0; q < TL; ++q) {
-      const int i = ty + 16 * p, t = tx + 16 * q;
-      const float v = (i < k && t < k) ? G[i * k + t] : 0.f;
-      a[p][q] = v;
-      if (i == t && i < k) tr += v;
-    }
-  tr = block_sum_f(tr, red);
-  const float shift = tr > 0.f ? ldexpf(tr / (float)k, -20) : 1e-30f;
-#pragma unroll
-  for (int p = 0; p < TL; ++p)
-#pragma unroll
-    for (int q = 0; q < TL; ++q)
-      if (ty + 16 * p == tx + 16 * q) a[p][q] += shift;
-  // ------------------------------------------------------------ Cholesky
-  for (int j = 0; j < k; ++j) {
-    const int rj = j & 15, qj = j >> 4;
-    float* col = buf[j & 1];
-    if (tx == rj) {
-#pragma unroll
-      for (int p = 0; p < TL; ++p) {
-        const int i = ty + 16 * p;
-        float v = 0.f;
-#pragma unroll
-        for (int qq = 0; qq < TL; ++qq)
-          if (qq == qj) v = a[p][qq];
-        if (i >= j && i < k) col[i] = v;
-        if (i == j) {
-          float piv = v;
-          if (!(piv > 0.f)) {
-            piv = shift;
-            atomicAdd(&flags[1], 1);
-          }
-          col[128] = piv;
-        }
-      }
-    }
-    __syncthreads();
-    const float piv = col[128];
-    const float rinv = 1.f / piv;
-    float ci[TL], ct[TL];
-#pragma unroll
-    for (int p = 0; p < TL; ++p) {
-      const int i = ty + 16 * p;
-      ci[p] = (i > j && i < k) ? col[i] : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < TL; ++q) {
-      const int t = tx + 16 * q;
-      ct[q] = (t > j && t < k) ? col[t] * rinv : 0.f;
-    }
-#pragma unroll
-    for (int p = 0; p < TL; ++p)
-#pragma unroll
-      for (int q = 0; q < TL; ++q) a[p][q] = fmaf(-ci[p], ct[q], a[p][q]);
-    if (tx == rj) {
-      const float rs = rsqrtf(piv);
-#pragma unroll
-      for (int p = 0; p < TL; ++p) {
-        const int i = ty + 16 * p;
-        if (i > j && i < k) Lsm[j * LS + i] = col[i] * rs;
-      }
-    }
-    if (tid == 0) Lsm[j * LS + j] = sqrtf(piv);
-  }
-  __syncthreads();
-  // ------------------------------------------- inverse: L X = I, B in a[][]
-#pragma unroll
-  for (int p = 0; p < TL; ++p)
-#pragma unroll
-    for (int q = 0; q < TL; ++q) a[p][q] = (ty + 16 * p == tx + 16 * q) ? 1.f : 0.f;
-  for (int j = 0; j < k; ++j) {
-    const int rj = j & 15, qj = j >> 4;
-    float* row = buf[j & 1];
-    const float ljj_inv = 1.f / Lsm[j * LS + j];
-    if (ty == rj) {
-#pragma unroll
-      for (int q = 0; q < TL; ++q) {
-        const int c = tx + 16 * q;
-        float v = 0.f;
-#pragma unroll
-        for (int pp = 0; pp < TL; ++pp)
-          if (pp == qj) v = a[pp][q];
-        if (c <= j) row[c] = v;
-        // row j is final: X[j][c] = B[j][c] / L[j][j]
-#pragma unroll
-        for (int pp = 0; pp < TL; ++pp)
-          if (pp == qj) a[pp][q] = v * ljj_inv;
-      }
-    }
-    __syncthreads();
-    float li[TL], rc[TL];
-#pragma unroll
-    for (int p = 0; p < TL; ++p) {
-      const int i = ty + 16 * p;
-      li[p] = (i > j && i < k) ? Lsm[j * LS + i] * ljj_inv : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < TL; ++q) {
-      const int c = tx + 16 * q;
-      rc[q] = c <= j ? row[c] : 0.f;
-    }
-#pragma unroll
-    for (int p = 0; p < TL; ++p)
-#pragma unroll
-      for (int q = 0; q < TL; ++q) a[p][q] = fmaf(-li[p], rc[q], a[p][q]);
-  }
-  // Rinv = X^T : Rinv[c][i] = X[i][c] for c <= i
-#pragma unroll
-  for (int p = 0; p < TL; ++p)
-#pragma unroll
-    for (int q = 0; q < TL; ++q) {
-      const int i = ty + 16 * p, c = tx + 16 * q;
-      if (i < k && c < k) Rinv[c * k + i] = c <= i ? a[p][q] : 0.f;
-    }
-}
 
 // ------------------------------------------------------- shrink weights
 __global__ void k_shrink_weights(const float* __restrict__ evals, const float* __restrict__ evecs,
@@ -534,13 +399,13 @@ void gram(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace
     nchunks = 0;
   }
   int64_t ne = (int64_t)n * n;
-  k_gram_reduce<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(partial, nchunks, npairs, ntiles, n, G);
+  k_gram_reduce<<<(unsigned)((ne + 31) / 32), 32 * kRedGroups, 0, s>>>(partial, nchunks, npairs, ntiles, n, G);
   SFD_LAUNCH_CHECK();
 }
 
 void gram_reduce_tiles(const float* partial, int nchunks, int n, float* G, cudaStream_t s) {
   int64_t ne = (int64_t)n * n;
-  k_gram_reduce<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(partial, nchunks, 1, 1, n, G);
+  k_gram_reduce<<<(unsigned)((ne + 31) / 32), 32 * kRedGroups, 0, s>>>(partial, nchunks, 1, 1, n, G);
   SFD_LAUNCH_CHECK();
 }
 
@@ -554,33 +419,7 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
 
 void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s) {
   if (k <= 128) {
-    static unsigned reg_attr = 0;  // one bit per device
-    int dv = 0;
-    SFD_CUDA(cudaGetDevice(&dv));
-    const int bytes_max = 128 * 129 * (int)sizeof(float);
-    if (dv < 32 && !(reg_attr & (1u << dv))) {
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      SFD_CUDA(cudaFuncSetAttribute(k_chol_inv_reg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_max));
-      reg_attr |= 1u << dv;
-    }
-    const size_t bytes = (size_t)k * (k + 1) * sizeof(float);
-    switch ((k + 15) / 16) {
-      case 1: k_chol_inv_reg<1><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 2: k_chol_inv_reg<2><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 3: k_chol_inv_reg<3><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 4: k_chol_inv_reg<4><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 5: k_chol_inv_reg<5><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 6: k_chol_inv_reg<6><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      case 7: k_chol_inv_reg<7><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-      default: k_chol_inv_reg<8><<<1, 256, bytes, s>>>(G, k, Rinv, flags); break;
-    }
-    SFD_LAUNCH_CHECK();
+    chol_inv_blk(G, k, Rinv, flags, s);
     return;
   }
   const int lda = k | 1;

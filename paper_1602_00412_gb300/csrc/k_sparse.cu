@@ -348,25 +348,45 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Sum of the partial rows of each split segment. One block per segment
+// (grid-stride): warp g adds partials g, g+8, ..., and the 8 warp sums are
+// combined in a fixed order. A hot column of the CSC copy has thousands of
+// partials, so the sum is spread over the block instead of one warp's chain.
+constexpr int kFixWarps = 8;
+
 template <int VPL>
-__global__ void k_spmm_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
-                             const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
-                             const float4* __restrict__ partial, int ldy4, int nvec,
-                             float4* __restrict__ Y) {
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= *n_split_ptr) return;
-  int seg = split_seg[w], f = split_first[w], c = split_count[w];
+__global__ void __launch_bounds__(32 * kFixWarps)
+    k_spmm_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
+                 const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
+                 const float4* __restrict__ partial, int ldy4, int nvec, float4* __restrict__ Y) {
+  __shared__ float4 sums[kFixWarps][32 * VPL];
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+  const int n_split = *n_split_ptr;
+  for (int w = blockIdx.x; w < n_split; w += gridDim.x) {
+    const int seg = split_seg[w], f = split_first[w], c = split_count[w];
 #pragma unroll
-  for (int q = 0; q < VPL; ++q) {
-    int vi = lane + 32 * q;
-    if (vi >= nvec) continue;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int t = 0; t < c; ++t) {
-      float4 p = partial[(int64_t)(f + t) * ldy4 + vi];
-      a.x += p.x; a.y += p.y; a.z += p.z; a.w += p.w;
+    for (int q = 0; q < VPL; ++q) {
+      const int vi = lane + 32 * q;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (vi < nvec) {
+        for (int t = wg; t < c; t += kFixWarps) {
+          const float4 p = partial[(int64_t)(f + t) * ldy4 + vi];
+          a.x += p.x; a.y += p.y; a.z += p.z; a.w += p.w;
+        }
+      }
+      sums[wg][vi] = a;
     }
-    Y[(int64_t)seg * ldy4 + vi] = a;
+    __syncthreads();
+    for (int vi = threadIdx.x; vi < nvec; vi += blockDim.x) {
+      float4 a = sums[0][vi];
+#pragma unroll
+      for (int g = 1; g < kFixWarps; ++g) {
+        const float4 p = sums[g][vi];
+        a.x += p.x; a.y += p.y; a.z += p.z; a.w += p.w;
+      }
+      Y[(int64_t)seg * ldy4 + vi] = a;
+    }
+    __syncthreads();
   }
 }
 
@@ -394,14 +414,21 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// One warp per split segment (grid-stride): lane-strided partial sums, then a
+// fixed shuffle tree.
 __global__ void k_spmv_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
                              const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
                              const float* __restrict__ partial, float* __restrict__ y) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= *n_split_ptr) return;
-  float a = 0.f;
-  for (int t = 0; t < split_count[w]; ++t) a += partial[split_first[w] + t];
-  y[split_seg[w]] = a;
+  const int lane = threadIdx.x & 31;
+  const int n_split = *n_split_ptr;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_split; w += nwarps) {
+    const int f = split_first[w], c = split_count[w];
+    float a = 0.f;
+    for (int t = lane; t < c; t += 32) a += partial[f + t];
+    a = warp_sum(a);
+    if (lane == 0) y[split_seg[w]] = a;
+  }
 }
 
 }  // namespace
@@ -504,13 +531,15 @@ void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float
                                       (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
                                       (float4*)partial);
   SFD_LAUNCH_CHECK();
-  const int g2 = (w.cap_split + 7) / 8;
+  const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));
   if (nvec <= 32)
-    k_spmm_fixup<1><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split,
-                                       (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+    k_spmm_fixup<1><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,
+                                                  w.d_n_split, (const float4*)partial, ldy / 4,
+                                                  nvec, (float4*)Y);
   else
-    k_spmm_fixup<2><<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split,
-                                       (const float4*)partial, ldy / 4, nvec, (float4*)Y);
+    k_spmm_fixup<2><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,
+                                                  w.d_n_split, (const float4*)partial, ldy / 4,
+                                                  nvec, (float4*)Y);
   SFD_LAUNCH_CHECK();
 }
 
@@ -519,8 +548,9 @@ void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s
   k_spmv<<<(w.cap_items + 7) / 8, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
                                                w.d_n_items, x, y, partial);
   SFD_LAUNCH_CHECK();
-  k_spmv_fixup<<<(w.cap_split + 127) / 128, 128, 0, s>>>(w.split_seg, w.split_first,
-                                                         w.split_count, w.d_n_split, partial, y);
+  const int g2 = std::max(1, std::min((w.cap_split + 7) / 8, 2 * 152));
+  k_spmv_fixup<<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split, partial,
+                                  y);
   SFD_LAUNCH_CHECK();
 }
 

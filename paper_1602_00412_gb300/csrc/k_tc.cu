@@ -98,30 +98,45 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 
+// Asynchronous global -> shared copies (cp.async): bytes beyond src_bytes are
+// zero-filled, and src_bytes = 0 reads nothing.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
 // ------------------------------------------------------------------ Gram
 // partial[chunk] (128 x 128 row-major; only the leading n x n block is
 // written) = X[rows of chunk, 0:n]^T X[rows of chunk, 0:n]. Rows are staged
-// 32 at a time (K = 32: four MMAs) into two buffers; a buffer is refilled once
-// the MMAs that read it have completed. Staging: a thread gathers one column
-// m of four consecutive rows (coalesced across the warp) and stores them as
-// one 16-byte row of a core matrix, so eight lanes fill one core (conflict free).
+// 32 at a time (K = 32: four MMAs) through a ring of kGSt buffers filled by
+// cp.async, kGSt - 1 stages ahead of the MMAs; a buffer is refilled once the
+// MMAs that read it have completed (its mbarrier). Element (m, k) of a stage
+// is X[row k][column m], four consecutive rows per 16-byte core row.
 constexpr int kGK = 32;             // rows per stage
 constexpr int kGTile = 128 * kGK;   // floats per stage
-constexpr int kGramSmem = 48 * 1024;  // 2 stages (32 KB) padded: at most 4 CTAs (512 TMEM columns) per SM
+constexpr int kGSt = 4;             // stages in the ring
+constexpr int kGramSmem = kGSt * kGTile * (int)sizeof(float);  // 64 KB: <= 3 CTAs per SM
 constexpr int kGramChunks = 152;
 
 __global__ void __launch_bounds__(kTcThreads)
-    k_tc_gram(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
-              int64_t rows_per_chunk, float* __restrict__ partial, int* __restrict__ flags) {
+    k_tc_gram(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_chunk,
+              float* __restrict__ partial, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[kGSt];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = map.total();
   if (warp == 0) tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    for (int b = 0; b < kGSt; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[b])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
@@ -131,58 +146,72 @@ __global__ void __launch_bounds__(kTcThreads)
   const uint32_t idesc = idesc_tf32(128, 128);
   const int64_t r_beg = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r_end = min(rows, r_beg + rows_per_chunk);
-  uint32_t phase[2] = {0u, 0u};
-  int used[2] = {0, 0};
-  bool ok = true;
-  int stage = 0;
-  for (int64_t r0 = r_beg; r0 < r_end; r0 += kGK, ++stage) {
-    const int b = stage & 1;
-    float* tile = smem + b * kGTile;
-    if (used[b]) {  // the MMAs issued on this buffer two stages ago must be done
-      const bool w = mbar_wait(&mbar[b], phase[b]);
-      if (!__syncthreads_and(w)) { ok = false; break; }
-      phase[b] ^= 1u;
-    }
-#pragma unroll 2
-    for (int it = 0; it < (kGK / 4) * 128 / kTcThreads; ++it) {
-      const int i = tid + it * kTcThreads;
-      const int m = i & 127, kc = i >> 7;  // column of X, group of 4 rows
-      float v[4];
+  const int nst = r_end > r_beg ? (int)((r_end - r_beg + kGK - 1) / kGK) : 0;
+  const uint32_t sbase = smem_u32(smem);
+  // thread tid copies column m = tid of the 32 rows of a stage
+  const int m = tid;
+  auto issue = [&](int st) {
+    const int64_t r0 = r_beg + (int64_t)st * kGK;
+    const uint32_t dst = sbase + (uint32_t)((st % kGSt) * kGTile) * 4u;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t g = r0 + kc * 4 + j;
-        v[j] = (g < r_end && m < n) ? map.at(X, ldx, g, m) : 0.f;
-      }
-      *reinterpret_cast<float4*>(&tile[core_off(m, kc * 4, kGK)]) = make_float4(v[0], v[1], v[2], v[3]);
+    for (int k = 0; k < kGK; ++k) {
+      const int64_t g = r0 + k;
+      const bool ok = g < r_end && m < n;
+      cp_async4(dst + (uint32_t)core_off(m, k, kGK) * 4u, ok ? (const void*)(X + g * ldx + m) : X,
+                ok ? 4u : 0u);
     }
+  };
+  uint32_t phase_bits = 0, used_bits = 0;
+  bool ok = true;
+#pragma unroll
+  for (int st = 0; st < kGSt - 1; ++st) {
+    if (st < nst) issue(st);
+    cp_async_commit();
+  }
+  for (int st = 0; st < nst; ++st) {
+    const int ns = st + kGSt - 1;
+    if (ns < nst) {
+      const int b = ns % kGSt;
+      if (used_bits & (1u << b)) {  // the MMAs that read this buffer must be done
+        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+        if (!__syncthreads_and(w)) { ok = false; break; }
+        phase_bits ^= 1u << b;
+        used_bits &= ~(1u << b);
+      }
+      issue(ns);
+    }
+    cp_async_commit();
+    cp_async_wait<kGSt - 1>();  // this thread's copies of stage st have landed
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
+    const int b = st % kGSt;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::);
-      const uint32_t base = smem_u32(tile);
+      const uint32_t base = sbase + (uint32_t)(b * kGTile) * 4u;
 #pragma unroll
       for (int kk = 0; kk < kGK / 8; ++kk) {
         const uint64_t da = smem_desc(base + kk * 256, 128, kGK * 32);
-        mma_tf32(tmem, da, da, idesc, (stage > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, da, da, idesc, (st > 0 || kk > 0) ? 1u : 0u);
       }
       mma_commit(&mbar[b]);
     }
-    used[b] = 1;
+    used_bits |= 1u << b;
   }
-  if (ok && stage > 0) {  // the last commit tracks every MMA issued before it
-    const int b = (stage - 1) & 1;
-    ok = __syncthreads_and(mbar_wait(&mbar[b], phase[b]));
+  cp_async_wait<0>();
+  if (ok && nst > 0) {  // MMAs complete in order: the last commit covers all
+    const int b = (nst - 1) % kGSt;
+    ok = __syncthreads_and(mbar_wait(&mbar[b], (phase_bits >> b) & 1u));
   }
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
-    for (int b = 0; b < 2; ++b)  // bounded: let MMAs in flight finish before freeing
-      if (used[b]) mbar_wait(&mbar[b], phase[b]);
+    for (int b = 0; b < kGSt; ++b)  // bounded: let MMAs in flight finish before freeing
+      if (used_bits & (1u << b)) mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   __syncthreads();
   float* out = partial + (int64_t)blockIdx.x * (128 * 128);
-  const int m = warp * 32 + lane;
-  const bool have = ok && stage > 0;
+  const int row = warp * 32 + lane;
+  const bool have = ok && nst > 0;
   for (int c0 = 0; c0 < n; c0 += 16) {
     float v[16];
     if (have) {
@@ -191,10 +220,10 @@ __global__ void __launch_bounds__(kTcThreads)
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = 0.f;
     }
-    if (m < n) {
+    if (row < n) {
 #pragma unroll
       for (int j = 0; j < 16; j += 4)
-        *reinterpret_cast<float4*>(&out[m * 128 + c0 + j]) =
+        *reinterpret_cast<float4*>(&out[row * 128 + c0 + j]) =
             make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
     }
   }
@@ -205,74 +234,85 @@ __global__ void __launch_bounds__(kTcThreads)
 
 // ----------------------------------------------------------------- X * T
 // Y[rows, 0:kout] = X[rows, 0:n] T (T: n x kout, row-major). T^T (Np x Kp,
-// n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA; each 128-row
-// tile of X is staged (eight lanes fill one core matrix with 16-byte rows),
-// multiplied with Kp / 8 MMAs and written back from tensor memory, one row per
-// thread.
+// n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA. 128-row tiles
+// of X go through two cp.async buffers: the next tile is in flight while the
+// current one is multiplied (Kp / 8 MMAs) and written back from tensor memory
+// (one row per thread). VEC: X rows start 16-byte aligned (ldx % 4 == 0), so
+// each 16-byte core row is one copy; otherwise element by element.
+template <bool VEC>
 __global__ void __launch_bounds__(kTcThreads)
-    k_tc_gemm(const float* __restrict__ X, int ldx, ColMap map, int64_t rows,
+    k_tc_gemm(const float* __restrict__ X, int ldx, int n, int64_t rows,
               const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
               int ldy, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
-  float* Bs = smem;            // Np x Kp
-  float* As = smem + Np * Kp;  // 128 x Kp
+  float* Bs = smem;  // Np x Kp, then two 128 x Kp tiles of X
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = map.total();
   const int kc_n = Kp >> 2;  // 16-byte chunks along K
+  const uint32_t sB = smem_u32(Bs);
+  const uint32_t sA0 = sB + (uint32_t)(Np * Kp) * 4u;
+  const uint32_t tile_bytes = (uint32_t)(128 * Kp) * 4u;
   if (warp == 0) tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::);
   }
-  for (int i = tid; i < Np * kc_n; i += kTcThreads) {  // B(j, k) = T[k][j]
-    const int j = i % Np, kc = i / Np;
-    float v[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int k = kc * 4 + t;
-      v[t] = (k < n && j < kout) ? T[(int64_t)k * kout + j] : 0.f;
-    }
-    *reinterpret_cast<float4*>(&Bs[core_off(j, kc * 4, Kp)]) = make_float4(v[0], v[1], v[2], v[3]);
+  // B(j, k) = T[k][j]: consecutive threads take consecutive j (coalesced)
+  for (int i = tid; i < Np * Kp; i += kTcThreads) {
+    const int j = i % Np, k = i / Np;
+    const bool ok = k < n && j < kout;
+    cp_async4(sB + (uint32_t)core_off(j, k, Kp) * 4u, ok ? (const void*)(T + (int64_t)k * kout + j) : T,
+              ok ? 4u : 0u);
   }
+  auto issue = [&](int64_t t, int buf) {
+    const int64_t row0 = t * 128;
+    const uint32_t dst = sA0 + (uint32_t)buf * tile_bytes;
+    if (VEC) {
+      // eight consecutive threads fill one core matrix (8 rows x 16 bytes)
+      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
+        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
+        const int64_t g = row0 + r;
+        const int k = kc * 4;
+        const int nval = g < rows ? max(0, min(4, n - k)) : 0;
+        cp_async16(dst + (uint32_t)core_off(r, k, Kp) * 4u,
+                   nval > 0 ? (const void*)(X + g * ldx + k) : X, (uint32_t)nval * 4u);
+      }
+    } else {
+      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
+        const int r = i / Kp, k = i % Kp;
+        const int64_t g = row0 + r;
+        const bool ok = g < rows && k < n;
+        cp_async4(dst + (uint32_t)core_off(r, k, Kp) * 4u, ok ? (const void*)(X + g * ldx + k) : X,
+                  ok ? 4u : 0u);
+      }
+    }
+  };
+  const int64_t ntiles = (rows + 127) / 128;
+  int64_t t = blockIdx.x;
+  if (t < ntiles) issue(t, 0);
+  cp_async_commit();  // group: B + first tile
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_tf32(128, Np);
-  const int64_t ntiles = (rows + 127) / 128;
-  const bool vec = map.k1 == 0 && (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
   const bool vec_out = (ldy & 3) == 0 && ((uintptr_t)Y & 15) == 0;
   uint32_t phase = 0;
   bool ok = true;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t row0 = t * 128;
-    for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
-      const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
-      const int64_t g = row0 + r;
-      const int k = kc * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (g < rows) {
-        if (vec && k + 4 <= n) {
-          v = *reinterpret_cast<const float4*>(&X[g * ldx + k]);
-        } else {
-          v.x = k + 0 < n ? map.at(X, ldx, g, k + 0) : 0.f;
-          v.y = k + 1 < n ? map.at(X, ldx, g, k + 1) : 0.f;
-          v.z = k + 2 < n ? map.at(X, ldx, g, k + 2) : 0.f;
-          v.w = k + 3 < n ? map.at(X, ldx, g, k + 3) : 0.f;
-        }
-      }
-      *reinterpret_cast<float4*>(&As[core_off(r, k, Kp)]) = v;
-    }
+  for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) issue(tn, buf ^ 1);  // its buffer was read by MMAs already complete
+    cp_async_commit();
+    cp_async_wait<1>();  // everything but the newest group has landed
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::);
-      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      const uint32_t a0 = sA0 + (uint32_t)buf * tile_bytes;
       for (int kk = 0; kk < Kp / 8; ++kk) {
         const uint64_t da = smem_desc(a0 + kk * 256, 128, Kp * 32);
-        const uint64_t db = smem_desc(b0 + kk * 256, 128, Kp * 32);
+        const uint64_t db = smem_desc(sB + kk * 256, 128, Kp * 32);
         mma_tf32(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
       }
       mma_commit(&mbar);
@@ -284,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads)
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
     const int r = warp * 32 + lane;
-    const int64_t g = row0 + r;
+    const int64_t g = t * 128 + r;
     for (int c0 = 0; c0 < Np; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
@@ -302,8 +342,9 @@ __global__ void __launch_bounds__(kTcThreads)
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::);
-    __syncthreads();  // tensor memory and the A tile are free again
+    __syncthreads();  // tensor memory is free for the next tile's MMAs
   }
+  cp_async_wait<0>();
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
     mbar_wait(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
@@ -320,7 +361,8 @@ bool tc_supported(int n, int kout) { return n >= 1 && n <= 128 && kout >= 1 && k
 void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
              cudaStream_t s) {
   const int n = map.total();
-  if (!tc_supported(n, n)) throw CudaError{cudaErrorInvalidValue, "gram_tc: n > 128"};
+  if (!tc_supported(n, n) || map.k1 != 0)
+    throw CudaError{cudaErrorInvalidValue, "gram_tc: one block of at most 128 columns"};
   static std::atomic<unsigned> attr{0};
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
@@ -334,7 +376,7 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
   rpc = ((rpc + kGK - 1) / kGK) * kGK;
   nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
   if (rows > 0) {
-    k_tc_gram<<<nchunks, kTcThreads, kGramSmem, s>>>(X, ldx, map, rows, rpc, ws.gram_partial,
+    k_tc_gram<<<nchunks, kTcThreads, kGramSmem, s>>>(X, ldx, n, rows, rpc, ws.gram_partial,
                                                      ws.flags);
     SFD_LAUNCH_CHECK();
   } else {
@@ -347,21 +389,31 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
                 float* Y, int ldy, Workspace& ws, cudaStream_t s) {
   if (rows <= 0 || kout <= 0) return;
   const int n = map.total();
-  if (!tc_supported(n, kout)) throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: n or kout > 128"};
+  if (!tc_supported(n, kout) || map.k1 != 0)
+    throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: one block, n and kout at most 128"};
   const int Kp = (n + 7) & ~7;
   const int Np = (kout + 15) & ~15;
   static std::atomic<unsigned> attr{0};
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
+  const int max_bytes = (128 * 128 + 2 * 128 * 128) * (int)sizeof(float);  // 192 KB
   if (dev < 32 && !(attr.load() & (1u << dev))) {
-    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  2 * 128 * 128 * (int)sizeof(float)));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  max_bytes));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  max_bytes));
     attr.fetch_or(1u << dev);
   }
-  const size_t bytes = (size_t)(Np * Kp + 128 * Kp) * sizeof(float);
+  const size_t bytes = (size_t)(Np * Kp + 2 * 128 * Kp) * sizeof(float);
   const int64_t ntiles = (rows + 127) / 128;
-  const int grid = (int)std::min<int64_t>(ntiles, 2 * 152);
-  k_tc_gemm<<<grid, kTcThreads, bytes, s>>>(X, ldx, map, rows, T, kout, Kp, Np, Y, ldy, ws.flags);
+  const int grid = (int)std::min<int64_t>(ntiles, 152);
+  const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
+  if (vec)
+    k_tc_gemm<true><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
+                                                    ws.flags);
+  else
+    k_tc_gemm<false><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
+                                                     ws.flags);
   SFD_LAUNCH_CHECK();
 }
 
