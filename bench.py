@@ -52,6 +52,12 @@ def parse():
                     help="0: FP32 throughout; 1: tensor-core (TF32) Gram and X R^-1 in the "
                          "orthonormalisations of all but the last power iteration")
     ap.add_argument("--slots", type=int, default=0, help="buffers in flight (0: library default)")
+    ap.add_argument("--q-mode", default="fixed", choices=["fixed", "learned"],
+                    help="power count per buffer: the fixed schedule, or the learned predictor "
+                         "(trained before the timed region on labelled streams of other seeds)")
+    ap.add_argument("--train-rows", type=int, default=400_000,
+                    help="rows of each labelled training stream (learned q)")
+    ap.add_argument("--train-streams", type=int, default=2)
     return ap.parse_args()
 
 
@@ -234,8 +240,29 @@ def ours_arm(args, rank, world, local):
     ix_h = torch.from_numpy(X.indices).pin_memory().numpy()
     vv_h = torch.from_numpy(X.values).pin_memory().numpy()
     B_h = torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()
+    qinfo = None
+    if args.q_mode == "learned":
+        t0 = time.time()
+        feats, labels = [], []
+        for s in range(args.train_streams):
+            Xt = make_stream(args.train_rows, 1000 + s)
+            tc = sfd.SFD(d, ell, 1000 + s, q_mode=2, precision=args.precision, slots=args.slots)
+            tc.append(Xt.indptr, Xt.indices, Xt.values)
+            tc.sketch()
+            F, L, _ = tc.q_log()
+            tc.close()
+            feats.append(F)
+            labels.append(L)
+        F, L = np.concatenate(feats), np.concatenate(labels)
+        theta, loss = sfd.sfd_q_train(F, L, sfd.q_init_params(0), epochs=300, batch=8, lr=3e-3)
+        qinfo = {"train_buffers": int(len(L)), "labels": sorted(set(int(x) for x in L)),
+                 "train_loss": loss, "train_s": round(time.time() - t0, 1),
+                 "train_streams": "%d x %d rows, seeds 1000+" % (args.train_streams, args.train_rows)}
     ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1,
-                  precision=args.precision, slots=args.slots)
+                  precision=args.precision, slots=args.slots,
+                  q_mode=1 if args.q_mode == "learned" else 0)
+    if args.q_mode == "learned":
+        ctx.set_q_model(theta)
 
     def step_device():
         ctx.reset()
@@ -296,6 +323,7 @@ def ours_arm(args, rank, world, local):
            "dtype": "f32" if args.precision == 0 else "tf32+f32", "data": "synthetic",
            "config": {"workload": DESC, "rows": X.n, "d": d, "ell": ell, "nnz_per_rank": X.nnz,
                       "precision": ["fp32", "mixed-tf32"][args.precision],
+                      "q_mode": args.q_mode, "q_model": qinfo,
                       "buffers_per_step": st["buffers"], "attempts_per_step": st["attempts"],
                       "q_per_attempt": st["q_total"] / max(1, st["attempts"]),
                       "l2": "inputs larger than L2 (CSR stream %.0f MB per rank)" % (

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SFD_ABI_VERSION 1u
+#define SFD_ABI_VERSION 2u
 
 #define SFD_OK 0
 #define SFD_EINVAL 1   /* bad argument: l < 1, l > d, index outside [0,d), non-monotone indptr, NaN/Inf value, ... */
@@ -63,13 +63,23 @@ typedef struct sfd_options {
                            of every power iteration of Alg. 1 but the last form their Gram and
                            X R^-1 on tcgen05 tensor cores (TF32 inputs, FP32 accumulation);
                            every other stage stays FP32 */
-  int32_t q_mode;       /* 0: fixed schedule (default); 1: learned predictor set by sfd_set_q_model */
+  int32_t q_mode;       /* power count per buffer. 0: the fixed schedule (default); 1: learned:
+                           q = clamp(ceil(network(features) + q_margin), 1, q_fixed) with the
+                           network set by sfd_set_q_model (fixed schedule until one is set); a
+                           buffer whose attempt VerifySpectral rejects is retried with q_fixed;
+                           2: fixed schedule, and every buffer whose first attempt is accepted
+                           is labelled for training (sfd_q_log) */
   int32_t strict;       /* 1: a buffer left unverified makes sfd_append_rows return SFD_EVERIFY */
   int32_t inject_vs_fail; /* testing: force this many VerifySpectral verdicts to False (host-side) */
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the context creates its own */
   int32_t profile;      /* 1: time every sparse-product launch with CUDA events (sfd_stats.spmm_*) */
   int32_t slots;        /* buffers in flight: each slot runs one buffer's BoostedSparseShrink on its
                            own stream while DenseShrink folds finished buffers in order; 0: 3 */
+  float q_margin;       /* q_mode 1: added to the network's output before rounding up (default 1) */
+  float q_tau;          /* q_mode 2: a buffer's label is the smallest q of the ladder
+                           {1,2,3,4,6,8,11,16,23,32,45,64} below q_fixed whose attempt passes
+                           VerifySpectral and keeps ||P||_F^2 >= (1 - q_tau) times its value at
+                           q_fixed (same G); q_fixed if none does (default 1e-2) */
 } sfd_options;
 
 /* Counters of a context (Alg. 2 / Alg. 4 bookkeeping). */
@@ -103,6 +113,7 @@ typedef struct sfd_shrink_info {
   double logsum;        /* log ||C^p x|| of the last VerifySpectral */
   double fro2_a;        /* ||A'||_F^2 */
   double fro2_b;        /* ||B'||_F^2 */
+  double captured;      /* ||P||_F^2 = ||Z^T A'||_F^2, the energy the subspace Z captures */
 } sfd_shrink_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -187,6 +198,44 @@ int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* col
 /* Orthonormalise the columns of X (rows x k, leading dimension ld, device) in
  * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */
 int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
+
+/* ---------------------------------------------------------------- learned q
+ * The power count q of Alg. 1 is fixed by Sec. 3.2 only up to a constant, and
+ * Alg. 4 verifies every result; the learned form predicts q per buffer (no
+ * counterpart in the paper). The predictor is a 16 -> 64 -> 64 -> 1 ReLU
+ * network over SFD_QF buffer features; its SFD_QPARAMS float parameters are
+ * laid out as W1 [16][64] (input-major), b1[64], W2 [64][64] (input-major),
+ * b2[64], w3[64], b3. Features (all computed on the device):
+ *   0 1;  1 ln m / 10;  2 ln N / 20 (N = nnz);  3 ln d / 15;  4 l / 256;
+ *   5 ln(N/m) / 5;  6 ln(||A'||_F^2 / N) / 10;  7 max row norm^2 / ||A'||_F^2;
+ *   8 max column count / N;  9 sum of column counts^2 / N^2;
+ *  10 m * sum of row counts^2 / N^2 - 1;  11 ln q_fixed / 3;
+ *  12 ||S0||_F^2 / tr(S0)^2;  13 max diag(S0) / tr(S0)  (S0 = (A'G)^T (A'G),
+ *     G the start block of attempt 0);  14 ln(1 + N / (m l));
+ *  15 1 - (nonempty columns) / d.
+ * All arrays below are host memory; errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA. */
+#define SFD_QF 16
+#define SFD_QPARAMS 5313
+/* Use `params` (host, copied) for q_mode 1; NULL removes the model. */
+int sfd_set_q_model(sfd_ctx* ctx, const float* params);
+/* The label log of q_mode 2: up to `cap` rows of features (cap x 16), labels
+ * and the buffers' q_fixed (nullable); *n_out = rows logged so far. */
+int sfd_q_log(const sfd_ctx* ctx, int64_t cap, float* features, float* labels, int32_t* q_fixed,
+              int64_t* n_out);
+/* The features of one buffer (device CSR as in sfd_bssh_buffer, key (seed, b)). */
+int sfd_q_features(int64_t m, int64_t d, int32_t ell, const int32_t* rowptr, const int32_t* colidx,
+                   const float* vals, uint64_t seed, int64_t b, int32_t q_fixed, float* features);
+/* y[i] = network(features[i]) for n rows (n x 16). */
+int sfd_q_predict(int64_t n, const float* features, const float* params, float* y_out);
+/* Gradient (SFD_QPARAMS floats) of L = (1/2n) sum (network(features[i]) - targets[i])^2,
+ * and L (nullable). */
+int sfd_q_grad(int64_t n, const float* features, const float* targets, const float* params,
+               float* grad_out, float* loss_out);
+/* Adam (lr, betas 0.9 / 0.999, eps 1e-8) on L over `epochs` passes in minibatches of
+ * `batch` rows, each pass in an order drawn from `seed`; params is updated in place
+ * and *loss_out (nullable) is L of the result over all n rows. */
+int sfd_q_train(int64_t n, const float* features, const float* targets, int32_t epochs,
+                int32_t batch, float lr, uint64_t seed, float* params, float* loss_out);
 
 /* The two dense products of a CholeskyQR step (the GramSchmidt of Alg. 1):
  * G = X^T X (k x k row-major, leading dimension k) over X (rows x k, leading

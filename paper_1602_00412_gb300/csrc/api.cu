@@ -10,6 +10,7 @@
 // Every call drains the pipeline before it returns.
 #include <string.h>
 
+#include <cmath>
 #include <deque>
 #include <memory>
 #include <new>
@@ -22,6 +23,8 @@ namespace sfd {
 
 constexpr int kDefaultSlots = 3;
 constexpr int kMaxSlots = 8;
+// power counts tried when labelling a buffer for the learned form
+constexpr int kLadder[] = {1, 2, 3, 4, 6, 8, 11, 16, 23, 32, 45, 64};
 
 struct Ctx {
   sfd_options opt;
@@ -49,13 +52,19 @@ struct Ctx {
     int slot;
     int64_t b;
     int m;
-    int q;
+    int q;        // power count of the attempt in flight
     int r;
+    int q_fixed;  // the schedule's q (used by retries)
   };
   std::deque<Pend> fifo;
   int next_slot = 0;
   int64_t b = 0;
   int inject_left = 0;
+  // learned power count: network parameters (device) and the label log
+  float* qparams = nullptr;
+  bool has_qmodel = false;
+  std::vector<float> qlog_feat, qlog_label;
+  std::vector<int> qlog_qfixed;
   sfd_stats st{};
   std::string last_error;
 
@@ -125,6 +134,32 @@ void release_user_stream(Ctx& C) {
   }
 }
 
+// Training label of a buffer whose first attempt (q_fixed) was accepted: rerun
+// SparseShrink + VerifySpectral with the same G at each smaller q of the
+// ladder; the label is the smallest q that passes VerifySpectral and keeps
+// ||P||_F^2 within a fraction q_tau of the q_fixed run. The reruns come after
+// DenseShrink has read B'^T (enqueue_attempt waits for `freed`), so the sketch
+// is unchanged.
+void label_buffer(Ctx& C, Slot& S, const Ctx::Pend& e, const Verdict& v) {
+  const float* f = S.qfeat_host;  // features of attempt 0, copied before `done`
+  const int p = vs_steps(C.d, delta_br(C.opt.delta, e.b, 0));
+  int lab = e.q_fixed;
+  for (int q : kLadder) {
+    if (q >= e.q_fixed) break;
+    S.enqueue_attempt(e.m, q, C.seed, (uint64_t)e.b, 0, p, C.opt.verify);
+    SFD_CUDA(cudaEventSynchronize(S.done));
+    const Verdict& w = *S.verdict_host;
+    if (w.timeout) return;
+    if ((w.ok || !C.opt.verify) && w.captured >= (1.0 - C.opt.q_tau) * v.captured) {
+      lab = q;
+      break;
+    }
+  }
+  C.qlog_feat.insert(C.qlog_feat.end(), f, f + kQF);
+  C.qlog_label.push_back((float)lab);
+  C.qlog_qfixed.push_back(e.q_fixed);
+}
+
 // Read the verdict of the oldest closed buffer, retry it until accepted or
 // out of attempts, then queue its DenseShrink.
 int harvest_front(Ctx& C) {
@@ -156,6 +191,7 @@ int harvest_front(Ctx& C) {
       break;
     }
     e.r++;
+    e.q = e.q_fixed;  // a rejected attempt is retried on the fixed schedule
     S.enqueue_attempt(e.m, e.q, C.seed, (uint64_t)e.b, (uint64_t)e.r,
                       vs_steps(C.d, delta_br(C.opt.delta, e.b, e.r)), C.opt.verify);
   }
@@ -169,6 +205,8 @@ int harvest_front(Ctx& C) {
   S.freed_pending = true;
   C.st.buffers++;
   C.fifo.pop_front();
+  if (C.opt.q_mode == 2 && status == SFD_OK && e.r == 0 && !v.timeout && (v.ok || !C.opt.verify))
+    label_buffer(C, S, e, v);
   return status;
 }
 
@@ -216,9 +254,19 @@ int close_buffer(Ctx& C) {
   if (m >= C.ell) {
     S.build(m, C.pend_nnz);
     const int q = q_for(C.opt, m);
-    S.enqueue_attempt(m, q, C.seed, (uint64_t)C.b, 0, vs_steps(C.d, delta_br(C.opt.delta, C.b, 0)),
-                      C.opt.verify);
-    C.fifo.push_back({C.fill, C.b, m, q, 0});
+    QControl qc;
+    qc.q_fixed = q;
+    if (C.opt.q_mode == 1 && C.has_qmodel) {
+      qc.predict = true;
+      qc.params = C.qparams;
+      qc.margin = C.opt.q_margin;
+    } else if (C.opt.q_mode == 2) {
+      qc.features = true;
+    }
+    const int q_used = S.enqueue_attempt(m, q, C.seed, (uint64_t)C.b, 0,
+                                         vs_steps(C.d, delta_br(C.opt.delta, C.b, 0)),
+                                         C.opt.verify, &qc);
+    C.fifo.push_back({C.fill, C.b, m, q_used, 0, q});
   } else {
     // too few rows for SparseShrink: DenseShrink([B; A']) with A' dense
     status = drain(C);
@@ -265,6 +313,8 @@ void sfd_options_init(sfd_options* o) {
   o->c_q = 0.25;
   o->q_override = -1;
   o->retry_cap = 8;
+  o->q_margin = 1.0f;
+  o->q_tau = 1e-2f;
 }
 
 const char* sfd_strerror(int s) {
@@ -293,7 +343,8 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
   Ctx& C = ctx->c;
   if (opt) C.opt = *opt; else sfd_options_init(&C.opt);
   if (!(C.opt.delta > 0 && C.opt.delta < 1) || C.opt.c_q < 0 || C.opt.slots < 0 ||
-      (C.opt.precision != 0 && C.opt.precision != 1)) {
+      (C.opt.precision != 0 && C.opt.precision != 1) || C.opt.q_mode < 0 || C.opt.q_mode > 2 ||
+      !(C.opt.q_tau >= 0.f && C.opt.q_tau < 1.f) || !(C.opt.q_margin > -64.f && C.opt.q_margin < 64.f)) {
     delete ctx;
     return SFD_EINVAL;
   }
@@ -541,6 +592,43 @@ int sfd_reset(sfd_ctx* ctx) {
   } catch (const CudaError& e) {
     return from_cuda(&C, e);
   }
+}
+
+int sfd_set_q_model(sfd_ctx* ctx, const float* params) {
+  if (!ctx) return SFD_EINVAL;
+  Ctx& C = ctx->c;
+  try {
+    SFD_CUDA(cudaSetDevice(C.dev));
+    if (!params) {
+      C.has_qmodel = false;
+      return SFD_OK;
+    }
+    for (int i = 0; i < kQParams; ++i)
+      if (!std::isfinite(params[i])) return fail(&C, SFD_EINVAL, "non-finite model parameter");
+    drain(C);
+    if (!C.qparams) C.qparams = C.stage_arena.alloc<float>(kQParams);
+    SFD_CUDA(cudaMemcpy(C.qparams, params, kQParams * sizeof(float), cudaMemcpyHostToDevice));
+    C.has_qmodel = true;
+    return SFD_OK;
+  } catch (const CudaError& e) {
+    return from_cuda(&C, e);
+  }
+}
+
+int sfd_q_log(const sfd_ctx* ctx, int64_t cap, float* features, float* labels, int32_t* q_fixed,
+              int64_t* n_out) {
+  if (!ctx || !n_out || cap < 0) return SFD_EINVAL;
+  const Ctx& C = ctx->c;
+  const int64_t n = (int64_t)C.qlog_label.size();
+  *n_out = n;
+  const int64_t k = std::min(n, cap);
+  if (k > 0 && (!features || !labels)) return SFD_EINVAL;
+  for (int64_t i = 0; i < k; ++i) {
+    memcpy(features + i * kQF, C.qlog_feat.data() + i * kQF, kQF * sizeof(float));
+    labels[i] = C.qlog_label[i];
+    if (q_fixed) q_fixed[i] = C.qlog_qfixed[i];
+  }
+  return SFD_OK;
 }
 
 }  // extern "C"

@@ -103,7 +103,13 @@ Slot::Slot(int64_t d_, int ell_, int64_t cap_rows_, int64_t cap_nnz_, cudaStream
     ws.wpart = A.alloc<float>(512 * kMaxEll + kMaxEll + 512);
     fro2 = A.alloc<double>(1024 + 8);
     verdict_dev = A.alloc<Verdict>(1);
+    qfeat = A.alloc<float>(kQF);
+    qacc = A.alloc<unsigned>(kQAccWords);
+    qy = A.alloc<float>(1);
+    q_dev = A.alloc<int>(1);
     SFD_CUDA(cudaMallocHost(&verdict_host, sizeof(Verdict)));
+    SFD_CUDA(cudaMallocHost(&qfeat_host, kQF * sizeof(float)));
+    SFD_CUDA(cudaMallocHost(&q_host, sizeof(int)));
     SFD_CUDA(cudaMallocHost(&ptr_host, (cap_rows + 1) * sizeof(int)));
     SFD_CUDA(cudaDeviceSynchronize());
   } catch (...) {
@@ -120,8 +126,12 @@ void Slot::cleanup() {
   arena.release();
   if (verdict_host) cudaFreeHost(verdict_host);
   if (ptr_host) cudaFreeHost(ptr_host);
+  if (qfeat_host) cudaFreeHost(qfeat_host);
+  if (q_host) cudaFreeHost(q_host);
   verdict_host = nullptr;
   ptr_host = nullptr;
+  qfeat_host = nullptr;
+  q_host = nullptr;
   if (done) cudaEventDestroy(done);
   if (freed) cudaEventDestroy(freed);
   done = freed = nullptr;
@@ -198,7 +208,8 @@ void Slot::collect_profile() {
   ev_used = 0;
 }
 
-void Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify) {
+int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify,
+                          const QControl* qc) {
   // Alg. 1: G ~ N(0,1)^{d x l}; Y = orth(A' G); q x { W = orth(A'^T Y); Y = orth(A' W) }
   launch_gauss_fill(W, d, ell, ld, seed, b, r, 1, stream);
   // mixed precision: the orthonormalisations of every power iteration but the
@@ -206,8 +217,19 @@ void Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, 
   // pass on Z stay FP32, so the TF32 perturbation of the subspace is damped by
   // one more FP32 iteration and Z is orthonormal to FP32 accuracy
   spmm_timed(csr, W, Y, d);
-  orth_pass(Y, m, Y2, mixed && q > 0);
+  orth_pass(Y, m, Y2, mixed && q > 0);  // leaves S0 = (A'G)^T (A'G) in ws.small_a
   std::swap(Y, Y2);
+  if (qc && (qc->predict || qc->features)) {
+    q_features(csr, csc, d, ell, qc->q_fixed, fro2, ws.small_a, qfeat, qacc, stream);
+    SFD_CUDA(cudaMemcpyAsync(qfeat_host, qfeat, kQF * sizeof(float), cudaMemcpyDeviceToHost,
+                             stream));
+    if (qc->predict) {
+      predict_q(qc->params, qfeat, qc->margin, qc->q_fixed, qy, q_dev, stream);
+      SFD_CUDA(cudaMemcpyAsync(q_host, q_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      SFD_CUDA(cudaStreamSynchronize(stream));
+      q = *q_host;
+    }
+  }
   for (int t = 0; t < q; ++t) {
     const bool tc = mixed && t + 1 < q;
     spmm_timed(csc, Y, W, m);
@@ -233,10 +255,11 @@ void Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, 
     VsArgs a{&csr, &csc, Bpt, ld, ell, d, m, ws.scalars + kSscale, p, seed, b, r};
     verify_spectral(a, ws, stream);
   }
-  launch_verdict(fro2, ws.scalars, ws.flags, verify, verdict_dev, stream);
+  launch_verdict(fro2, ws.scalars, ws.flags, ws.evals, ell, verify, verdict_dev, stream);
   SFD_CUDA(cudaMemcpyAsync(verdict_host, verdict_dev, sizeof(Verdict), cudaMemcpyDeviceToHost,
                            stream));
   SFD_CUDA(cudaEventRecord(done, stream));
+  return q;
 }
 
 // ===================================================================== Merger

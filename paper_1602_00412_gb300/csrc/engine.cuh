@@ -42,6 +42,15 @@ struct DevArena {
 // Scratch of the dense stages (Gram, Cholesky, eigensolver, weights).
 void alloc_dense_scratch(DevArena& A, Workspace& ws);
 
+// How an attempt chooses its power count (the learned form; Alg. 1's q).
+struct QControl {
+  const float* params = nullptr;  // device network parameters (kQParams), predict only
+  float margin = 1.f;
+  int q_fixed = 0;
+  bool predict = false;   // q = network(features), clamped to [1, q_fixed]
+  bool features = false;  // compute the features (copied to qfeat_host) without predicting
+};
+
 struct Slot {
   int64_t d = 0, cap_rows = 0, cap_nnz = 0;
   int ell = 0, ld = 0;
@@ -60,6 +69,13 @@ struct Slot {
   double* fro2 = nullptr;       // [0] ||A'||_F^2, [1..] partials
   Verdict* verdict_dev = nullptr;
   Verdict* verdict_host = nullptr;  // pinned
+  // learned q: features and prediction of the current buffer
+  float* qfeat = nullptr;           // device, kQF
+  unsigned* qacc = nullptr;         // device, kQAccWords
+  float* qy = nullptr;              // device, 1
+  int* q_dev = nullptr;             // device, 1
+  float* qfeat_host = nullptr;      // pinned, kQF
+  int* q_host = nullptr;            // pinned, 1
   int* ptr_host = nullptr;          // pinned staging of the local row pointer
   // precision 1: the orthonormalisations inside the power iterations run their
   // Gram and X R^-1 on tensor cores (TF32 inputs, FP32 accumulate)
@@ -82,8 +98,12 @@ struct Slot {
   // CSR structure + CSC copy + work lists of the buffer already in csr.{ptr,idx,val}
   void build(int m, int64_t nnz);
   // One SparseShrink attempt (Alg. 3) + Delta + VerifySpectral (Alg. 6) +
-  // verdict copy; `done` is recorded at the end.
-  void enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify);
+  // verdict copy; `done` is recorded at the end. With qc->predict the power
+  // count comes from the network: the host waits for the first product's
+  // Gram and the prediction before it enqueues the power loop. Returns the q
+  // used.
+  int enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, int p, int verify,
+                      const QControl* qc = nullptr);
   void collect_profile();  // host: needs `done`
 
  private:

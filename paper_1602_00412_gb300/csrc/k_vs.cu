@@ -153,7 +153,8 @@ __global__ void k_delta(const double* __restrict__ fro2a, double* __restrict__ s
 }
 
 __global__ void k_verdict(const double* __restrict__ fro2a, const double* __restrict__ scal,
-                          const int* __restrict__ flags, int verify, Verdict* __restrict__ out) {
+                          const int* __restrict__ flags, const float* __restrict__ evals, int ell,
+                          int verify, Verdict* __restrict__ out) {
   Verdict v;
   v.fro2a = *fro2a;
   v.fro2b = scal[kSfro2b];
@@ -163,6 +164,9 @@ __global__ void k_verdict(const double* __restrict__ fro2a, const double* __rest
   v.logsum = v.small || v.zero ? -INFINITY : scal[kSlogsum];
   v.ok = !verify || v.small || v.zero || v.logsum <= 0.0;
   v.timeout = flags[2];
+  double c = 0.0;
+  for (int i = 0; i < ell; ++i) c += (double)evals[i];
+  v.captured = c;
   *out = v;
 }
 
@@ -173,9 +177,9 @@ void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s) {
   SFD_LAUNCH_CHECK();
 }
 
-void launch_verdict(const double* fro2a, const double* scal, const int* flags, int verify,
-                    Verdict* out, cudaStream_t s) {
-  k_verdict<<<1, 1, 0, s>>>(fro2a, scal, flags, verify, out);
+void launch_verdict(const double* fro2a, const double* scal, const int* flags,
+                    const float* evals, int ell, int verify, Verdict* out, cudaStream_t s) {
+  k_verdict<<<1, 1, 0, s>>>(fro2a, scal, flags, evals, ell, verify, out);
   SFD_LAUNCH_CHECK();
 }
 

@@ -112,7 +112,32 @@ int sfd_bssh_buffer(int64_t m, int64_t d, int32_t ell, const int32_t* rowptr, co
       info->logsum = v.logsum;
       info->fro2_a = v.fro2a;
       info->fro2_b = v.fro2b;
+      info->captured = v.captured;
     }
+    return SFD_OK;
+  } catch (const CudaError& e) {
+    return code_of(e);
+  }
+}
+
+int sfd_q_features(int64_t m, int64_t d, int32_t ell, const int32_t* rowptr, const int32_t* colidx,
+                   const float* vals, uint64_t seed, int64_t b, int32_t q_fixed, float* features) {
+  if (m < 1 || d < 1 || ell < 1 || ell > m || m > d || ell > kMaxEll || !rowptr || !features ||
+      b < 0 || q_fixed < 1)
+    return SFD_EINVAL;
+  try {
+    const int64_t nnz = checked_rowptr(rowptr, m, d);
+    if (nnz < 0 || (nnz > 0 && (!colidx || !vals))) return SFD_EINVAL;
+    Slot S(d, ell, m, nnz, nullptr);
+    if (!load_slot(S, m, nnz, rowptr, colidx, vals)) return SFD_EINVAL;
+    // S0 = (A'G)^T (A'G) for the G of attempt 0 (Alg. 1's start block)
+    launch_gauss_fill(S.W, d, ell, S.ld, seed, (uint64_t)b, 0, 1, S.stream);
+    spmm(S.csr, S.W, S.ld, S.ld, S.Y, S.ld, S.ws.partial_rows, S.stream);
+    gram(S.Y, S.ld, single_map(ell), m, S.ws.small_a, S.ws, S.stream);
+    q_features(S.csr, S.csc, d, ell, q_fixed, S.fro2, S.ws.small_a, S.qfeat, S.qacc, S.stream);
+    SFD_CUDA(cudaMemcpyAsync(features, S.qfeat, kQF * sizeof(float), cudaMemcpyDeviceToHost,
+                             S.stream));
+    SFD_CUDA(cudaStreamSynchronize(S.stream));
     return SFD_OK;
   } catch (const CudaError& e) {
     return code_of(e);

@@ -221,13 +221,36 @@ enum : int {
 // Verdict of one attempt, copied to pinned host memory.
 struct Verdict {
   double fro2a, fro2b, delta, logsum;
+  double captured;  // ||P||_F^2 = sum of the eigenvalues of P P^T
   int ok, small, zero, timeout;  // timeout: a bounded device wait expired (flags[2])
 };
 // Delta = (fro2a - fro2b) / (alpha l), scale = 2 / Delta, small flag.
 void launch_delta(const double* fro2a, double* scal, int ell, cudaStream_t s);
 // Verdict from the device scalars (verify = 0: accepted).
-void launch_verdict(const double* fro2a, const double* scal, const int* flags, int verify,
-                    Verdict* out,
+void launch_verdict(const double* fro2a, const double* scal, const int* flags,
+                    const float* evals, int ell, int verify, Verdict* out,
                     cudaStream_t s);
+
+// ------------------------------------------------------------- learned q
+constexpr int kQF = 16;   // features
+constexpr int kQH = 64;   // hidden width
+constexpr int kQParams = kQF * kQH + kQH + kQH * kQH + kQH + kQH + 1;
+constexpr int kQAccWords = 8;  // scratch of q_features (unsigned words)
+// The 16 features of a buffer (CSR + CSC built, fro2 = ||A'||_F^2 on the
+// device, S0 = Gram of A'G, l x l) into feat[16].
+void q_features(const Csr& csr, const Csr& csc, int64_t d, int ell, int q_fixed,
+                const double* fro2, const float* S0, float* feat, unsigned* acc_dev,
+                cudaStream_t s);
+// y[s] = network(X[s]) (X: n x 16 row-major).
+void mlp_forward(const float* P, const float* X, int n, float* y, cudaStream_t s);
+// q_out[0] = clamp(ceil(network(feat) + margin), 1, q_fixed); y_tmp: 1 float.
+void predict_q(const float* P, const float* feat, float margin, int q_fixed, float* y_tmp,
+               int* q_out, cudaStream_t s);
+// grad = d/dP of (1/2n) sum (network(X) - T)^2, loss (nullable) = that value.
+void mlp_grad(const float* P, const float* X, const float* T, int n, float* grad, float* loss,
+              cudaStream_t s);
+// Adam step number `step` (>= 1) on P with moments m1, m2.
+void adam_update(float* P, const float* grad, float* m1, float* m2, int step, float lr,
+                 cudaStream_t s);
 
 }  // namespace sfd

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libsfd.so")
 
-SFD_ABI_VERSION = 1
+SFD_ABI_VERSION = 2
 SFD_OK, SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA, SFD_EVERIFY, SFD_ETIMEOUT = 0, 1, 2, 3, 4, 5
 SFD_HOST, SFD_DEVICE = 0, 1
 
@@ -30,7 +30,7 @@ class sfd_options(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("q_mode", ctypes.c_int32),
                 ("strict", ctypes.c_int32), ("inject_vs_fail", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("slots", ctypes.c_int32)]
+                ("slots", ctypes.c_int32), ("q_margin", ctypes.c_float), ("q_tau", ctypes.c_float)]
 
 
 class sfd_stats(ctypes.Structure):
@@ -46,13 +46,15 @@ class sfd_shrink_info(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int32), ("attempts", ctypes.c_int32), ("verified", ctypes.c_int32),
                 ("vs_steps", ctypes.c_int32), ("delta_shrink", ctypes.c_double),
                 ("logsum", ctypes.c_double), ("fro2_a", ctypes.c_double),
-                ("fro2_b", ctypes.c_double)]
+                ("fro2_b", ctypes.c_double), ("captured", ctypes.c_double)]
 
 
 EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "sfd_merge",
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
            "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig",
-           "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts"]
+           "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_q_model", "sfd_q_log",
+           "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train"]
+QF, QPARAMS = 16, 5313
 
 _lib = None
 
@@ -91,6 +93,12 @@ def load(path=None):
     L.sfd_symeig_noalloc.argtypes = [i32, vp, i32, vp, vp]
     L.sfd_gram.argtypes = [i64, i32, vp, i32, vp, i32]
     L.sfd_gemm_ts.argtypes = [i64, i32, vp, i32, vp, i32, vp, i32, i32]
+    L.sfd_set_q_model.argtypes = [vp, vp]
+    L.sfd_q_log.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
+    L.sfd_q_features.argtypes = [i64, i64, i32, vp, vp, vp, u64, i64, i32, vp]
+    L.sfd_q_predict.argtypes = [i64, vp, vp, vp]
+    L.sfd_q_grad.argtypes = [i64, vp, vp, vp, vp, vp]
+    L.sfd_q_train.argtypes = [i64, vp, vp, i32, i32, ctypes.c_float, u64, vp, vp]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error"):
@@ -238,6 +246,65 @@ def sfd_symeig_noalloc(n, S, nwant, evals, evecs):
                                      ctypes.c_void_p(evecs.data_ptr())))
 
 
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _hptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else None
+
+
+def q_init_params(seed=0):
+    """Initial network parameters: He-scaled normal weights from a seeded
+    generator, zero biases, output bias 4 (a middle power count)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((QF, 64)) * np.sqrt(2.0 / QF)
+    W2 = rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64)
+    w3 = rng.standard_normal(64) * np.sqrt(1.0 / 64)
+    P = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [4.0]])
+    return P.astype(np.float32)
+
+
+def sfd_q_features(m, d, ell, rowptr, colidx, vals, seed, b, q_fixed):
+    out = np.empty(QF, dtype=np.float32)
+    _check(load().sfd_q_features(m, d, ell, ctypes.c_void_p(rowptr.data_ptr()),
+                                 ctypes.c_void_p(colidx.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                 seed, b, q_fixed, _hptr(out)))
+    return out
+
+
+def sfd_q_predict(features, params):
+    X = _f32(features).reshape(-1, QF)
+    P = _f32(params, QPARAMS)
+    y = np.empty(len(X), dtype=np.float32)
+    _check(load().sfd_q_predict(len(X), _hptr(X), _hptr(P), _hptr(y)))
+    return y
+
+
+def sfd_q_grad(features, targets, params):
+    X = _f32(features).reshape(-1, QF)
+    T = _f32(targets, len(X))
+    P = _f32(params, QPARAMS)
+    g = np.empty(QPARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().sfd_q_grad(len(X), _hptr(X), _hptr(T), _hptr(P), _hptr(g), ctypes.byref(loss)))
+    return float(loss.value), g
+
+
+def sfd_q_train(features, targets, params, epochs, batch, lr, seed=0):
+    """Adam on the squared error; returns (trained parameters, final loss)."""
+    X = _f32(features).reshape(-1, QF)
+    T = _f32(targets, len(X))
+    P = _f32(params, QPARAMS).copy()
+    loss = ctypes.c_float()
+    _check(load().sfd_q_train(len(X), _hptr(X), _hptr(T), int(epochs), int(batch), float(lr), seed,
+                              _hptr(P), ctypes.byref(loss)))
+    return P, float(loss.value)
+
+
 class SFD:
     """Stream object over one context: append rows, read the sketch, merge."""
 
@@ -259,6 +326,21 @@ class SFD:
 
     def stats(self):
         return sfd_get_stats(self.ctx)
+
+    def set_q_model(self, params):
+        P = None if params is None else _f32(params, QPARAMS)
+        _check(load().sfd_set_q_model(self.ctx, None if P is None else _hptr(P)), self.ctx)
+
+    def q_log(self):
+        """(features n x 16, labels n, q_fixed n) logged in q_mode 2."""
+        n = ctypes.c_int64()
+        _check(load().sfd_q_log(self.ctx, 0, None, None, None, ctypes.byref(n)))
+        F = np.empty((n.value, QF), dtype=np.float32)
+        lab = np.empty(n.value, dtype=np.float32)
+        qf = np.empty(n.value, dtype=np.int32)
+        if n.value:
+            _check(load().sfd_q_log(self.ctx, n.value, _hptr(F), _hptr(lab), _hptr(qf), ctypes.byref(n)))
+        return F, lab, qf
 
     def reset(self):
         sfd_reset(self.ctx)

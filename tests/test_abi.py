@@ -42,6 +42,8 @@ def test_options_defaults(lib):
     assert o.abi_version == sfd.SFD_ABI_VERSION
     assert (o.delta, o.verify, o.c_q, o.q_override, o.retry_cap) == (0.01, 1, 0.25, -1, 8)
     assert o.cuda_stream is None
+    assert (o.precision, o.q_mode, o.slots) == (0, 0, 0)
+    assert o.q_margin == 1.0 and abs(o.q_tau - 1e-2) < 1e-9
 
 
 def test_create_rejects_bad_shapes_without_gpu(lib):
