@@ -199,6 +199,36 @@ int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* col
  * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */
 int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
 
+/* ------------------------------------------------------------ many streams
+ * A batch of independent SFD streams on the current device (Alg. 2 each;
+ * no counterpart in the paper beyond mergeability, Sec. 3.1): stream i has
+ * d[i] columns, l = ell[i], Philox seed `seed + i`, and the options `opt`
+ * (NULL: defaults; cuda_stream must be NULL; slots 0 means 1 here). Worker
+ * threads (`workers`, 0: min(nstreams, 8)) drive the streams so that their
+ * buffers run concurrently; stream i belongs to worker i % workers, so its
+ * rows are processed in append order. Host arrays are copied before
+ * sfd_batch_append returns; device arrays are read later and must stay valid
+ * until sfd_batch_wait (or a call that waits) returns. Errors of queued work
+ * are reported by the next call that waits (first error only). */
+typedef struct sfd_batch sfd_batch;
+int sfd_batch_create(int32_t nstreams, const int64_t* d, const int32_t* ell, uint64_t seed,
+                     const sfd_options* opt, int32_t workers, sfd_batch** out);
+/* Queue rows for one stream (arguments as in sfd_append_rows). */
+int sfd_batch_append(sfd_batch* batch, int32_t stream, int64_t nrows, const int64_t* indptr,
+                     const int32_t* indices, const float* values, int where);
+/* Wait for all queued work. */
+int sfd_batch_wait(sfd_batch* batch);
+/* Wait, then the sketch of one stream (as sfd_sketch). */
+int sfd_batch_sketch(sfd_batch* batch, int32_t stream, float* B_out, int where);
+/* Chunk-parallel sketch: wait, then fold every stream into stream 0 by a
+ * binary tree of merges (level s merges stream i + s into stream i for i a
+ * multiple of 2s, pairs of a level in parallel); all streams must have the same
+ * d and l. Streams other than 0 keep partial unions. B_out (nullable) gets
+ * stream 0's sketch (l x d row-major, where as in sfd_sketch). */
+int sfd_batch_merge_tree(sfd_batch* batch, float* B_out, int where);
+int sfd_batch_stats(const sfd_batch* batch, int32_t stream, sfd_stats* out);
+void sfd_batch_destroy(sfd_batch* batch);
+
 /* ---------------------------------------------------------------- learned q
  * The power count q of Alg. 1 is fixed by Sec. 3.2 only up to a constant, and
  * Alg. 4 verifies every result; the learned form predicts q per buffer (no

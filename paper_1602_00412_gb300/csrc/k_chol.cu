@@ -37,15 +37,16 @@ __global__ void __launch_bounds__(kCThreads)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   // G's entries arrive by cp.async (all in flight at once); padding is the identity
-  for (int e = tid; e < KP * KP; e += kCThreads) {
-    const int i = e / KP, j = e - (e / KP) * KP;
-    if (i < k && j < k) {
-      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&A[i * LD + j]);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + (int64_t)i * k + j));
-    } else {
-      A[i * LD + j] = (i == j) ? 1.f : 0.f;
+  for (int i = warp; i < KP; i += kCThreads / 32)
+    for (int j = lane; j < KP; j += 32) {
+      if (i < k && j < k) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&A[i * LD + j]);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst),
+                     "l"(G + (int64_t)i * k + j));
+      } else {
+        A[i * LD + j] = (i == j) ? 1.f : 0.f;
+      }
     }
-  }
   asm volatile("cp.async.commit_group;" ::);
   asm volatile("cp.async.wait_group 0;" ::);
   __syncthreads();
@@ -74,13 +75,15 @@ __global__ void __launch_bounds__(kCThreads)
 #pragma unroll
       for (int t = 0; t < kCB; ++t) d[t] = A[(j0 + i) * LD + j0 + t];
       int clamped = 0;
+      float rdiag[kCB];  // 1 / L[j][j], the same in every lane
 #pragma unroll
       for (int j = 0; j < kCB; ++j) {
         float piv = __shfl_sync(kFull, d[j], j);
         clamped += !(piv > 0.f);
         piv = piv > 0.f ? piv : shift;
-        const float ljj = sqrtf(piv), inv = 1.f / ljj;
-        const float lij = i > j ? d[j] * inv : (i == j ? ljj : 0.f);
+        const float inv = rsqrtf(piv);  // hardware reciprocal square root
+        rdiag[j] = inv;
+        const float lij = i > j ? d[j] * inv : (i == j ? piv * inv : 0.f);
         d[j] = lij;
 #pragma unroll
         for (int t = 0; t < kCB; ++t) {
@@ -98,8 +101,7 @@ __global__ void __launch_bounds__(kCThreads)
         float s = r == i ? 1.f : 0.f;
 #pragma unroll
         for (int t = 0; t < r; ++t) s = fmaf(-__shfl_sync(kFull, d[t], r), x[t], s);
-        const float lrr = __shfl_sync(kFull, d[r], r);
-        x[r] = r >= i ? s / lrr : 0.f;
+        x[r] = r >= i ? s * rdiag[r] : 0.f;
       }
       if (lane < kCB) {
 #pragma unroll
@@ -175,9 +177,16 @@ __global__ void __launch_bounds__(kCThreads)
       const int jb = e >> 8, rr = (e >> 4) & 15, cc = e & 15;
       const int ib = jb + dl;
       const int row = ib * kCB + rr, col = jb * kCB + cc;
-      float s = 0.f;
-      for (int t = col; t < ib * kCB; ++t) s = fmaf(A[row * LD + t], Li[t * LD + col], s);
-      S[e] = s;
+      // t over blocks jb .. ib-1 (Li[t][col] is 0 above the diagonal of block jb)
+      float s0 = 0.f, s1 = 0.f;
+      for (int t0 = jb * kCB; t0 < ib * kCB; t0 += kCB) {
+#pragma unroll
+        for (int t = 0; t < kCB; t += 2) {
+          s0 = fmaf(A[row * LD + t0 + t], Li[(t0 + t) * LD + col], s0);
+          s1 = fmaf(A[row * LD + t0 + t + 1], Li[(t0 + t + 1) * LD + col], s1);
+        }
+      }
+      S[e] = s0 + s1;
     }
     __syncthreads();
     for (int e = tid; e < nout; e += kCThreads) {
@@ -185,17 +194,16 @@ __global__ void __launch_bounds__(kCThreads)
       const int ib = jb + dl;
       const int row = ib * kCB + rr, col = jb * kCB + cc;
       float s = 0.f;
-      for (int u = 0; u <= rr; ++u)
+#pragma unroll
+      for (int u = 0; u < kCB; ++u)  // Li[row][ib*16 + u] is 0 for u > rr
         s = fmaf(Li[row * LD + ib * kCB + u], S[(jb << 8) + (u << 4) + cc], s);
       Li[row * LD + col] = -s;
     }
     __syncthreads();
   }
   // Rinv = (L^-1)^T, upper triangular
-  for (int e = tid; e < k * k; e += kCThreads) {
-    const int c = e / k, i = e - (e / k) * k;
-    Rinv[e] = c <= i ? Li[i * LD + c] : 0.f;
-  }
+  for (int c = warp; c < k; c += kCThreads / 32)
+    for (int i = lane; i < k; i += 32) Rinv[c * k + i] = c <= i ? Li[i * LD + c] : 0.f;
 }
 
 }  // namespace

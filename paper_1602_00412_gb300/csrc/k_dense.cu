@@ -7,6 +7,7 @@
 //  - shrink weights sqrt(1 - lambda_l^2 / lambda_i^2) (Alg. 3 / Alg. 5)
 // All arithmetic is fp32; the small k x k factorisations live in one CTA.
 #include <algorithm>
+#include <atomic>
 
 #include "sfd_internal.cuh"
 
@@ -425,13 +426,13 @@ void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaS
   const int lda = k | 1;
   size_t bytes = (size_t)k * lda * sizeof(float);
   int use_smem = bytes <= 200 * 1024;
-  static unsigned attr_set = 0;  // one bit per device
+  static std::atomic<unsigned> attr_set{0};  // one bit per device
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
-  if (dev < 32 && !(attr_set & (1u << dev))) {
+  if (dev < 32 && !(attr_set.load() & (1u << dev))) {
     SFD_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
-    attr_set |= 1u << dev;
+    attr_set.fetch_or(1u << dev);
   }
   k_chol_inv<<<1, kCholThreads, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags, use_smem);
   SFD_LAUNCH_CHECK();

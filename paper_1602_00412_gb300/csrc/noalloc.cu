@@ -17,8 +17,10 @@ namespace {
 
 constexpr int kNoAllocMaxN = 256;
 
-// symeig_work_floats(256, 256): reflectors n*n, betas n, six n x nwant blocks,
-// and an n x (n|1) matrix when it does not fit in shared memory (~2.1 MB).
+// An upper bound of symeig_work_floats(256, 256), the eigensolver's scratch
+// for n = nwant = 256 (reflectors, eigenvector blocks, Gram and factor, an
+// n x (n|1) matrix when it does not fit in shared memory), ~2.1 MB; every
+// call checks the bound.
 constexpr size_t kNoAllocFloats = (size_t)kNoAllocMaxN * kNoAllocMaxN + kNoAllocMaxN +
                                   6 * (size_t)kNoAllocMaxN * kNoAllocMaxN +
                                   (size_t)kNoAllocMaxN * (kNoAllocMaxN | 1);

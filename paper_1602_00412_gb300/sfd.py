@@ -53,7 +53,9 @@ EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "s
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
            "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig",
            "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_q_model", "sfd_q_log",
-           "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train"]
+           "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train", "sfd_batch_create",
+           "sfd_batch_append", "sfd_batch_wait", "sfd_batch_sketch", "sfd_batch_merge_tree",
+           "sfd_batch_stats", "sfd_batch_destroy"]
 QF, QPARAMS = 16, 5313
 
 _lib = None
@@ -99,9 +101,18 @@ def load(path=None):
     L.sfd_q_predict.argtypes = [i64, vp, vp, vp]
     L.sfd_q_grad.argtypes = [i64, vp, vp, vp, vp, vp]
     L.sfd_q_train.argtypes = [i64, vp, vp, i32, i32, ctypes.c_float, u64, vp, vp]
+    L.sfd_batch_create.argtypes = [i32, vp, vp, u64, ctypes.POINTER(sfd_options), i32,
+                                   ctypes.POINTER(vp)]
+    L.sfd_batch_append.argtypes = [vp, i32, i64, vp, vp, vp, ctypes.c_int]
+    L.sfd_batch_wait.argtypes = [vp]
+    L.sfd_batch_sketch.argtypes = [vp, i32, vp, ctypes.c_int]
+    L.sfd_batch_merge_tree.argtypes = [vp, vp, ctypes.c_int]
+    L.sfd_batch_stats.argtypes = [vp, i32, ctypes.POINTER(sfd_stats)]
+    L.sfd_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
         fn = getattr(L, name)
-        if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error"):
+        if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error",
+                        "sfd_batch_destroy"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -349,6 +360,76 @@ class SFD:
         if self.ctx is not None:
             sfd_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent SFD streams driven concurrently (sfd_batch_*): stream i has
+    d[i] columns, l = ell[i] and seed `seed + i`."""
+
+    def __init__(self, d, ell, seed=0, workers=0, **opts):
+        self.d = [int(x) for x in d]
+        self.ell = [int(x) for x in ell]
+        da = np.asarray(self.d, dtype=np.int64)
+        ea = np.asarray(self.ell, dtype=np.int32)
+        o = options(**opts) if opts else None
+        h = ctypes.c_void_p()
+        _check(load().sfd_batch_create(len(da), _hptr(da), _hptr(ea), seed,
+                                       ctypes.byref(o) if o is not None else None, int(workers),
+                                       ctypes.byref(h)))
+        self.h = h
+        self._keep = []  # device arrays the workers have not read yet
+
+    def append(self, stream, indptr, indices, values):
+        pi, w1 = _ptr(indptr, np.int64)
+        px, w2 = _ptr(indices, np.int32)
+        pv, w3 = _ptr(values, np.float32)
+        if not (w1 == w2 == w3):
+            raise TypeError("indptr, indices and values must all be host or all device arrays")
+        if w1 == SFD_DEVICE:
+            self._keep.append((indptr, indices, values))
+        _check(load().sfd_batch_append(self.h, int(stream), len(indptr) - 1, pi, px, pv, w1))
+
+    def wait(self):
+        try:
+            _check(load().sfd_batch_wait(self.h))
+        finally:
+            self._keep.clear()
+
+    def sketch(self, stream, out=None):
+        if out is None:
+            out = np.empty((self.ell[stream], self.d[stream]), dtype=np.float32)
+        p, w = _ptr(out, np.float32)
+        try:
+            _check(load().sfd_batch_sketch(self.h, int(stream), p, w))
+        finally:
+            self._keep.clear()
+        return out
+
+    def merge_tree(self, out=None):
+        if out is None:
+            out = np.empty((self.ell[0], self.d[0]), dtype=np.float32)
+        p, w = _ptr(out, np.float32)
+        try:
+            _check(load().sfd_batch_merge_tree(self.h, p, w))
+        finally:
+            self._keep.clear()
+        return out
+
+    def stats(self, stream):
+        s = sfd_stats()
+        _check(load().sfd_batch_stats(self.h, int(stream), ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in sfd_stats._fields_}
+
+    def close(self):
+        if self.h is not None:
+            load().sfd_batch_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
