@@ -193,17 +193,25 @@ def peaks():
 
 
 def traffic_record():
-    """dram bytes per launch of the SpMM kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
-    p = os.path.join(ROOT, "profiles", "spmm_c2_traffic.json")
+    """DRAM bytes per launch of the SpMM stage from the committed ncu summary
+    (profiles/spmm_c2_traffic.md, lines "source_sha <hex>" and
+    "dram_bytes_per_launch <n>"), valid only while the kernel source is
+    unchanged; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "spmm_c2_traffic.md")
+    rec = {}
     try:
         with open(p) as f:
-            j = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                parts = line.strip().strip("`").split()
+                if len(parts) == 2 and parts[0] in ("source_sha", "dram_bytes_per_launch"):
+                    rec[parts[0]] = parts[1]
+    except OSError:
         return None
     src = os.path.join(ROOT, "paper_1602_00412_gb300", "csrc", "k_sparse.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return j.get("bytes_per_launch") if j.get("source_sha") == h else None
+    if rec.get("source_sha") != h or "dram_bytes_per_launch" not in rec:
+        return None
+    return float(rec["dram_bytes_per_launch"])
 
 
 # ------------------------------------------------------------------ arms

@@ -515,10 +515,10 @@ int sfd_sketch(sfd_ctx* ctx, float* B_out, int where) {
     if (where == SFD_DEVICE) {
       transpose(M.B(), C.d, C.ell, M.ld, B_out, C.d, M.stream);
     } else {
-      float* tmp = C.slots[0]->W2;  // d x ld scratch holds the l x d sketch
-      SFD_CUDA(cudaStreamSynchronize(C.slots[0]->stream));
-      transpose(M.B(), C.d, C.ell, M.ld, tmp, C.d, M.stream);
-      SFD_CUDA(cudaMemcpyAsync(B_out, tmp, (size_t)C.ell * C.d * sizeof(float),
+      // the Merger's own l x d buffer: slot buffers are not scratch (their
+      // padding columns must stay zero)
+      transpose(M.B(), C.d, C.ell, M.ld, M.out, C.d, M.stream);
+      SFD_CUDA(cudaMemcpyAsync(B_out, M.out, (size_t)C.ell * C.d * sizeof(float),
                                cudaMemcpyDeviceToHost, M.stream));
     }
     SFD_CUDA(cudaStreamSynchronize(M.stream));

@@ -87,6 +87,10 @@ Slot::Slot(int64_t d_, int ell_, int64_t cap_rows_, int64_t cap_nnz_, cudaStream
     Bpt = A.alloc<float>(dense_d);
     Y = A.alloc<float>(dense_m);
     Y2 = A.alloc<float>(dense_m);
+    Wh = A.alloc<__half>(dense_d);
+    Yh = A.alloc<__half>(dense_m);
+    SFD_CUDA(cudaMemset(Wh, 0, dense_d * sizeof(__half)));
+    SFD_CUDA(cudaMemset(Yh, 0, dense_m * sizeof(__half)));
     for (float* p : {W, W2, Bpt}) SFD_CUDA(cudaMemset(p, 0, dense_d * sizeof(float)));
     for (float* p : {Y, Y2}) SFD_CUDA(cudaMemset(p, 0, dense_m * sizeof(float)));
     alloc_dense_scratch(A, ws);
@@ -163,19 +167,24 @@ void Slot::build(int m, int64_t nnz) {
   build_work(csc, stream);
 }
 
-void Slot::orth_pass(const float* X, int64_t rows, float* Xout, bool tc) {
+bool Slot::orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half* Xh) {
   const ColMap map = single_map(ell);
   tc = tc && tc_supported(ell, ell);
   if (tc) gram_tc(X, ld, map, rows, ws.small_a, ws, stream);
   else gram(X, ld, map, rows, ws.small_a, ws, stream);
   chol_inv(ws.small_a, ell, ws.small_b, ws.eig_work, ws.flags, stream);
-  if (tc) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream);
+  if (tc) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, Xh);
   else gemm_ts(X, ld, map, rows, ws.small_b, ell, Xout, ld, stream);
+  return tc && Xh;
 }
 
-void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in) {
+void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in, const __half* Xh) {
+  auto run = [&] {
+    if (Xh) spmm_h(c, Xh, ld, ld, Yo, ld, ws.partial_rows, stream);
+    else spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream);
+  };
   if (!profile) {
-    spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream);
+    run();
     return;
   }
   if (ev_used + 2 > (int)ev_pool.size()) {
@@ -188,10 +197,11 @@ void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in) 
   const int i0 = ev_used;
   ev_used += 2;
   SFD_CUDA(cudaEventRecord(ev_pool[i0], stream));
-  spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream);
+  run();
   SFD_CUDA(cudaEventRecord(ev_pool[i0 + 1], stream));
-  const double bytes = 8.0 * (double)c.nnz + 4.0 * (c.nseg + 1) + 4.0 * ell * (double)rows_in +
-                       4.0 * ell * (double)c.nseg;
+  const double in_bytes = Xh ? 2.0 : 4.0;
+  const double bytes = 8.0 * (double)c.nnz + 4.0 * (c.nseg + 1) +
+                       in_bytes * ell * (double)rows_in + 4.0 * ell * (double)c.nseg;
   ev_pending.push_back({i0, bytes});
 }
 
@@ -216,9 +226,13 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
   // last run on tensor cores; the last iteration and the second CholeskyQR
   // pass on Z stay FP32, so the TF32 perturbation of the subspace is damped by
   // one more FP32 iteration and Z is orthonormal to FP32 accuracy
+  // Mixed precision also stores the orthonormal blocks between a tensor-core
+  // orthonormalisation and the next sparse product as fp16 (|entries| <= 1,
+  // the TF32 inputs' precision), so the product's gather moves half the bytes.
   spmm_timed(csr, W, Y, d);
-  orth_pass(Y, m, Y2, mixed && q > 0);  // leaves S0 = (A'G)^T (A'G) in ws.small_a
-  std::swap(Y, Y2);
+  // leaves S0 = (A'G)^T (A'G) in ws.small_a
+  bool y_half = orth_pass(Y, m, Y2, mixed && q > 0, Yh);
+  if (!y_half) std::swap(Y, Y2);
   if (qc && (qc->predict || qc->features)) {
     q_features(csr, csc, d, ell, qc->q_fixed, fro2, ws.small_a, qfeat, qacc, stream);
     SFD_CUDA(cudaMemcpyAsync(qfeat_host, qfeat, kQF * sizeof(float), cudaMemcpyDeviceToHost,
@@ -232,13 +246,15 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
   }
   for (int t = 0; t < q; ++t) {
     const bool tc = mixed && t + 1 < q;
-    spmm_timed(csc, Y, W, m);
-    orth_pass(W, d, W2, tc);
-    std::swap(W, W2);
-    spmm_timed(csr, W, Y, d);
-    orth_pass(Y, m, Y2, tc);
-    std::swap(Y, Y2);
+    spmm_timed(csc, Y, W, m, y_half ? Yh : nullptr);
+    const bool w_half = orth_pass(W, d, W2, tc, Wh);
+    if (!w_half) std::swap(W, W2);
+    spmm_timed(csr, W, Y, d, w_half ? Wh : nullptr);
+    y_half = orth_pass(Y, m, Y2, tc, Yh);
+    if (!y_half) std::swap(Y, Y2);
   }
+  // here Y is fp32: a tensor-core first pass implies q >= 1 (the predicted q
+  // is at least 1 as well), and the last iteration is fp32
   orth_pass(Y, m, Y2, false);  // second CholeskyQR pass on Z
   std::swap(Y, Y2);
   // Alg. 3: P^T = A'^T Z, svd(P, l) through P P^T, B'^T = P^T H diag(s)
@@ -270,6 +286,7 @@ Merger::Merger(int64_t d_, int ell_) {
   try {
     SFD_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) Bt[i] = arena.alloc<float>((size_t)d * ld);
+    out = arena.alloc<float>((size_t)d * ell);
     alloc_dense_scratch(arena, ws);
     zero();
     SFD_CUDA(cudaStreamSynchronize(stream));

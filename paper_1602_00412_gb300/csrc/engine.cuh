@@ -64,6 +64,7 @@ struct Slot {
   int *key = nullptr, *key2 = nullptr, *a_alt = nullptr;
   float* b_alt = nullptr;
   float *W = nullptr, *W2 = nullptr, *Y = nullptr, *Y2 = nullptr;
+  __half *Wh = nullptr, *Yh = nullptr;  // fp16 copies of orthonormal blocks (mixed precision)
   float* Bpt = nullptr;         // B'^T, d x ld
   Workspace ws;
   double* fro2 = nullptr;       // [0] ||A'||_F^2, [1..] partials
@@ -108,8 +109,11 @@ struct Slot {
 
  private:
   void cleanup();
-  void orth_pass(const float* X, int64_t rows, float* Xout, bool tc);
-  void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in);
+  // CholeskyQR step X -> Xout; with tc and Xh, the result goes to Xh as fp16
+  // only (returns true then)
+  bool orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half* Xh = nullptr);
+  void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in,
+                  const __half* Xh = nullptr);
 };
 
 struct Merger {
@@ -118,6 +122,7 @@ struct Merger {
   cudaStream_t stream = nullptr;
   DevArena arena;
   float* Bt[2] = {nullptr, nullptr};  // d x ld
+  float* out = nullptr;               // l x d: the sketch, transposed for a host copy
   int cur = 0;
   Workspace ws;
 

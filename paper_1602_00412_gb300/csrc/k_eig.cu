@@ -76,9 +76,20 @@ __device__ void tri_solve_scaled(const float* U0, const float* U1, const float* 
     Z[i * nwp] = ri;
     Z[(i + 1) * nwp] = rn - Lm[i * nwp] * ri;
   }
+  // back substitution; near a cluster the solution can outgrow fp32, so when
+  // an entry passes 2^100 the whole system (solved part, neighbours and the
+  // remaining right-hand side) is scaled by 2^-100 and the entry redone
   float zmax = 0.f, z1 = 0.f, z2 = 0.f;
   for (int i = n - 1; i >= 0; --i) {
     float z = (Z[i * nwp] - U1[i * nwp] * z1 - U2[i * nwp] * z2) / U0[i * nwp];
+    if (!(fabsf(z) <= 0x1p100f)) {
+      for (int k = 0; k < n; ++k) Z[k * nwp] *= 0x1p-100f;
+      z1 *= 0x1p-100f;
+      z2 *= 0x1p-100f;
+      zmax *= 0x1p-100f;
+      z = (Z[i * nwp] - U1[i * nwp] * z1 - U2[i * nwp] * z2) / U0[i * nwp];
+      if (!(fabsf(z) <= 0x1p100f)) z = 0.f;
+    }
     Z[i * nwp] = z;
     z2 = z1;
     z1 = z;
@@ -335,7 +346,13 @@ __global__ void k_inviter(const float* __restrict__ dg, const float* __restrict_
   tri_factor(d, e, lam, U0, U1, U2, Lm, P, n, vpc, tiny_piv);
   for (int i = 0; i < n; ++i) Zs[i * vpc] = hash_unit(i, j);
   for (int it = 0; it < 3; ++it) tri_solve_scaled(U0, U1, U2, Lm, P, Zs, n, vpc);
-  for (int i = 0; i < n; ++i) Z[(size_t)i * nwp + j] = Zs[i * vpc];
+  // an iterate that collapsed (zero or non-finite) restarts as the hash
+  // vector; the orthonormalisation then takes its component off the others
+  float nz = 0.f;
+  for (int i = 0; i < n; ++i) nz = fmaf(Zs[i * vpc], Zs[i * vpc], nz);
+  const bool bad = !(nz > 0.f) || !isfinite(nz);
+  for (int i = 0; i < n; ++i)
+    Z[(size_t)i * nwp + j] = bad ? hash_unit(i, j) * rsqrtf((float)n) : Zs[i * vpc];
 }
 
 // 4. CholeskyQR of the eigenvector block Z (n x nwant, row-major, ld nwp):

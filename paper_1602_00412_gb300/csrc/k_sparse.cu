@@ -348,6 +348,67 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Y = A X with X in fp16 (k <= 128 columns, rows of ldx halves, ldx % 8 == 0):
+// a warp takes one work item; its two half-warps take alternate entries, each
+// lane loads 8 columns (16 bytes) of the gathered row, so the L2 gather moves
+// half the bytes of the fp32 kernel. Sums are fp32; the two halves are added
+// in a fixed order at the end.
+template <int U>
+__global__ void __launch_bounds__(256)
+    k_spmm_h(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
+             const int2* __restrict__ items, const int* __restrict__ item_slot,
+             const int* __restrict__ n_items_ptr, const uint4* __restrict__ X, int ldx8, int nv8,
+             float4* __restrict__ Y, int ldy4, float4* __restrict__ partial) {
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  if (item >= *n_items_ptr) return;
+  const int2 it = items[item];
+  const int seg = it.x, beg = it.y;
+  const int end = min(beg + kSplit, ptr[seg + 1]);
+  float acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+  for (int p = beg; p < end; p += 32) {
+    const int cnt = min(32, end - p);
+    const int c_l = lane < cnt ? idx[p + lane] : 0;
+    const float v_l = lane < cnt ? val[p + lane] : 0.f;
+    for (int jj = 0; jj < cnt; jj += 2 * U) {
+      int cu[U];
+      float vu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = jj + 2 * u + half;  // this half-warp's entry
+        cu[u] = __shfl_sync(0xffffffffu, c_l, e & 31);
+        const float vv = __shfl_sync(0xffffffffu, v_l, e & 31);
+        vu[u] = e < cnt ? vv : 0.f;       // past cnt: column 0 times 0
+      }
+      if (hl < nv8) {
+        uint4 xs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xs[u] = __ldg(&X[(int64_t)cu[u] * ldx8 + hl]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const __half2* h = reinterpret_cast<const __half2*>(&xs[u]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __half22float2(h[q]);
+            acc[2 * q] = fmaf(vu[u], f.x, acc[2 * q]);
+            acc[2 * q + 1] = fmaf(vu[u], f.y, acc[2 * q + 1]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
+  if (half == 0 && hl < nv8) {
+    const int slot = item_slot[item];
+    float4* out = slot < 0 ? Y + (int64_t)seg * ldy4 : partial + (int64_t)slot * ldy4;
+    out[2 * hl] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    out[2 * hl + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  }
+}
+
 // Sum of the partial rows of each split segment. One block per segment
 // (grid-stride): warp g adds partials g, g+8, ..., and the 8 warp sums are
 // combined in a fixed order. A hot column of the CSC copy has thousands of
@@ -396,17 +457,27 @@ __global__ void __launch_bounds__(256)
            const int2* __restrict__ items, const int* __restrict__ item_slot,
            const int* __restrict__ n_items_ptr, const float* __restrict__ x, float* __restrict__ y,
            float* __restrict__ partial) {
-  int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (item >= *n_items_ptr) return;
-  int2 it = items[item];
-  int seg = it.x, beg = it.y;
-  int end = min(beg + kSplit, ptr[seg + 1]);
+  // eight lanes per work item (four items per warp): rows and columns of a
+  // buffer hold tens of entries, so a whole warp per item would idle
+  const int n_items = *n_items_ptr;
+  const int warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3;
+  if (warp_first >= n_items) return;  // whole warp past the end
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int gl = threadIdx.x & 7;
+  const bool live = item < n_items;
   float a = 0.f;
-  for (int p = beg + lane; p < end; p += 32) a = fmaf(val[p], __ldg(&x[idx[p]]), a);
-  a = warp_sum(a);
-  if (lane == 0) {
-    int slot = item_slot[item];
+  int seg = 0;
+  if (live) {
+    const int2 it = items[item];
+    seg = it.x;
+    const int end = min(it.y + kSplit, ptr[seg + 1]);
+    for (int p = it.y + gl; p < end; p += 8) a = fmaf(val[p], __ldg(&x[idx[p]]), a);
+  }
+  a += __shfl_xor_sync(0xffffffffu, a, 4);
+  a += __shfl_xor_sync(0xffffffffu, a, 2);
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  if (live && gl == 0) {
+    const int slot = item_slot[item];
     if (slot < 0)
       y[seg] = a;
     else
@@ -543,10 +614,34 @@ void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float
   SFD_LAUNCH_CHECK();
 }
 
+void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, float* partial,
+            cudaStream_t s) {
+  if (k > 128 || (ldx & 7) || (ldy & 7))
+    throw CudaError{cudaErrorInvalidValue, "spmm_h: k <= 128, ldx and ldy multiples of 8"};
+  const SegWork& w = c.work;
+  const int nv8 = (k + 7) / 8;
+  const int grid = (w.cap_items + 7) / 8;
+  k_spmm_h<4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                   reinterpret_cast<const uint4*>(X), ldx / 8, nv8, (float4*)Y,
+                                   ldy / 4, (float4*)partial);
+  SFD_LAUNCH_CHECK();
+  const int nvec = 2 * nv8;  // float4 columns written per row
+  const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));
+  if (nvec <= 32)
+    k_spmm_fixup<1><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,
+                                                  w.d_n_split, (const float4*)partial, ldy / 4,
+                                                  nvec, (float4*)Y);
+  else
+    k_spmm_fixup<2><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,
+                                                  w.d_n_split, (const float4*)partial, ldy / 4,
+                                                  nvec, (float4*)Y);
+  SFD_LAUNCH_CHECK();
+}
+
 void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s) {
   const SegWork& w = c.work;
-  k_spmv<<<(w.cap_items + 7) / 8, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
-                                               w.d_n_items, x, y, partial);
+  k_spmv<<<(w.cap_items + 31) / 32, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
+                                                 w.d_n_items, x, y, partial);
   SFD_LAUNCH_CHECK();
   const int g2 = std::max(1, std::min((w.cap_split + 7) / 8, 2 * 152));
   k_spmv_fixup<<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split, partial,

@@ -16,6 +16,8 @@
 #include <atomic>
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "sfd_internal.cuh"
 
 namespace sfd {
@@ -243,7 +245,7 @@ template <bool VEC>
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_gemm(const float* __restrict__ X, int ldx, int n, int64_t rows,
               const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
-              int ldy, int* __restrict__ flags) {
+              int ldy, __half* __restrict__ Yh, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
   float* Bs = smem;  // Np x Kp, then two 128 x Kp tiles of X
   __shared__ __align__(8) uint64_t mbar;
@@ -328,7 +330,18 @@ __global__ void __launch_bounds__(kTcThreads)
     for (int c0 = 0; c0 < Np; c0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (g < rows) {
+      if (g < rows && Yh) {  // fp16 copy only (|entries| <= 1: columns are orthonormal)
+        __half* y = Yh + g * ldy + c0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 8) {
+          __half2 h[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            h[q] = __floats2half2_rn(c0 + j + 2 * q < kout ? v[j + 2 * q] : 0.f,
+                                     c0 + j + 2 * q + 1 < kout ? v[j + 2 * q + 1] : 0.f);
+          if (c0 + j + 8 <= ldy) *reinterpret_cast<uint4*>(&y[j]) = *reinterpret_cast<const uint4*>(h);
+        }
+      } else if (g < rows) {
         float* y = Y + g * ldy + c0;
         if (vec_out && c0 + 16 <= kout) {
 #pragma unroll
@@ -386,11 +399,13 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
 }
 
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
-                float* Y, int ldy, Workspace& ws, cudaStream_t s) {
+                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh) {
   if (rows <= 0 || kout <= 0) return;
   const int n = map.total();
   if (!tc_supported(n, kout) || map.k1 != 0)
     throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: one block, n and kout at most 128"};
+  if (Yh && ((ldy & 7) != 0 || ((uintptr_t)Yh & 15) != 0 || ldy < kout))
+    throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: fp16 output needs ld % 8 == 0, 16-byte rows"};
   const int Kp = (n + 7) & ~7;
   const int Np = (kout + 15) & ~15;
   static std::atomic<unsigned> attr{0};
@@ -410,10 +425,10 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
   const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
   if (vec)
     k_tc_gemm<true><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
-                                                    ws.flags);
+                                                    Yh, ws.flags);
   else
     k_tc_gemm<false><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
-                                                     ws.flags);
+                                                     Yh, ws.flags);
   SFD_LAUNCH_CHECK();
 }
 

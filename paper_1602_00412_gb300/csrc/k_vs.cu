@@ -76,24 +76,46 @@ __global__ void k_scale(float* __restrict__ x, int64_t n, const double* __restri
     x[i] *= s;
 }
 
-// wpart[b][c] = sum over the rows j of stripe b of Bt[j][c] * x[j]
+// wpart[b][c] = sum over the rows j of stripe b of Bt[j][c] * x[j]. A warp
+// reads a row of B'^T as float4 lanes (ld % 4 == 0); the 8 warps of a block
+// take rows j = warp, warp + 8, ... of the stripe, four at a time, and their
+// partial sums are added in warp order (fixed).
 __global__ void __launch_bounds__(256)
     k_btx_partial(const float* __restrict__ Bt, int ld, int ell, int64_t d,
                   const float* __restrict__ x, float* __restrict__ wpart) {
-  const int c = threadIdx.x;
+  __shared__ float4 red[8][kMaxEll / 4];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int nvec = (ell + 3) >> 2;
   const int64_t rows = (d + gridDim.x - 1) / gridDim.x;
   const int64_t j0 = blockIdx.x * rows, j1 = min(d, j0 + rows);
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  if (c < ell) {
-    int64_t j = j0;
-    for (; j + 4 <= j1; j += 4) {
-      a0 = fmaf(Bt[(j + 0) * ld + c], x[j + 0], a0);
-      a1 = fmaf(Bt[(j + 1) * ld + c], x[j + 1], a1);
-      a2 = fmaf(Bt[(j + 2) * ld + c], x[j + 2], a2);
-      a3 = fmaf(Bt[(j + 3) * ld + c], x[j + 3], a3);
+  const float4* B4 = reinterpret_cast<const float4*>(Bt);
+  const int ld4 = ld >> 2;
+  for (int c4 = lane; c4 < (kMaxEll / 4); c4 += 32) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c4 < nvec) {
+      int64_t j = j0 + wp;
+      for (; j + 24 < j1; j += 32) {  // four rows of this warp in flight
+        const float4 b0 = B4[(j + 0) * ld4 + c4], b1 = B4[(j + 8) * ld4 + c4];
+        const float4 b2 = B4[(j + 16) * ld4 + c4], b3 = B4[(j + 24) * ld4 + c4];
+        const float x0 = x[j], x1 = x[j + 8], x2 = x[j + 16], x3 = x[j + 24];
+        a.x = fmaf(b0.x, x0, a.x); a.y = fmaf(b0.y, x0, a.y); a.z = fmaf(b0.z, x0, a.z); a.w = fmaf(b0.w, x0, a.w);
+        a.x = fmaf(b1.x, x1, a.x); a.y = fmaf(b1.y, x1, a.y); a.z = fmaf(b1.z, x1, a.z); a.w = fmaf(b1.w, x1, a.w);
+        a.x = fmaf(b2.x, x2, a.x); a.y = fmaf(b2.y, x2, a.y); a.z = fmaf(b2.z, x2, a.z); a.w = fmaf(b2.w, x2, a.w);
+        a.x = fmaf(b3.x, x3, a.x); a.y = fmaf(b3.y, x3, a.y); a.z = fmaf(b3.z, x3, a.z); a.w = fmaf(b3.w, x3, a.w);
+      }
+      for (; j < j1; j += 8) {
+        const float4 b0 = B4[j * ld4 + c4];
+        const float x0 = x[j];
+        a.x = fmaf(b0.x, x0, a.x); a.y = fmaf(b0.y, x0, a.y); a.z = fmaf(b0.z, x0, a.z); a.w = fmaf(b0.w, x0, a.w);
+      }
     }
-    for (; j < j1; ++j) a0 = fmaf(Bt[j * ld + c], x[j], a0);
-    wpart[blockIdx.x * ell + c] = (a0 + a1) + (a2 + a3);
+    red[wp][c4] = a;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ell; c += blockDim.x) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += reinterpret_cast<const float*>(&red[w][0])[c];
+    wpart[blockIdx.x * ell + c] = t;
   }
 }
 
@@ -114,24 +136,52 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block (fixed grid)
+// v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block
+// (fixed grid). A warp reads a row as float4 lanes and takes four rows at a
+// time (independent loads in flight); lane 0 keeps the block's rows' squares
+// in row order.
 __global__ void __launch_bounds__(256)
     k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
                const float* __restrict__ w, float* __restrict__ part) {
-  __shared__ float ws[kMaxEll];
+  __shared__ float4 ws[kMaxEll / 4];
   __shared__ float red[8];
-  for (int c = threadIdx.x; c < ell; c += blockDim.x) ws[c] = w[c];
+  const int nvec = (ell + 3) >> 2;
+  for (int c = threadIdx.x; c < kMaxEll / 4; c += blockDim.x) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * c + 0 < ell) t.x = w[4 * c + 0];
+    if (4 * c + 1 < ell) t.y = w[4 * c + 1];
+    if (4 * c + 2 < ell) t.z = w[4 * c + 2];
+    if (4 * c + 3 < ell) t.w = w[4 * c + 3];
+    ws[c] = t;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const float4* B4 = reinterpret_cast<const float4*>(Bt);
+  const int ld4 = ld >> 2;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
   float acc2 = 0.f;
-  for (int64_t j = (int64_t)blockIdx.x * 8 + wp; j < d; j += (int64_t)gridDim.x * 8) {
-    float s = 0.f;
-    for (int c = lane; c < ell; c += 32) s = fmaf(Bt[j * ld + c], ws[c], s);
-    s = warp_sum(s);
-    float nv = v[j] - s;
+  for (int64_t j = ((int64_t)blockIdx.x * 8 + wp) * 4; j < d; j += nwarps * 4) {
+    float s[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float t = 0.f;
+      if (j + r < d)
+        for (int c4 = lane; c4 < nvec; c4 += 32) {
+          const float4 b = B4[(j + r) * ld4 + c4], q = ws[c4];
+          t = fmaf(b.x, q.x, fmaf(b.y, q.y, fmaf(b.z, q.z, fmaf(b.w, q.w, t))));
+        }
+      s[r] = t;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s[r] = warp_sum(s[r]);
     if (lane == 0) {
-      v[j] = nv;
-      acc2 = fmaf(nv, nv, acc2);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (j + r < d) {
+          const float nv = v[j + r] - s[r];
+          v[j + r] = nv;
+          acc2 = fmaf(nv, nv, acc2);
+        }
     }
   }
   if (lane == 0) red[wp] = acc2;

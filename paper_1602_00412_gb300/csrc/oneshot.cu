@@ -16,6 +16,17 @@ int code_of(const CudaError& e) {
   return e.err == cudaErrorMemoryAllocation ? SFD_ENOMEM : SFD_ECUDA;
 }
 
+// Order a library stream after the work the caller queued on the legacy
+// default stream (e.g. the fill of an output or input array).
+void after_caller(cudaStream_t s) {
+  cudaEvent_t ev;
+  SFD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e1 = cudaEventRecord(ev, 0);
+  cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, ev, 0) : e1;
+  cudaEventDestroy(ev);
+  if (e2 != cudaSuccess) throw CudaError{e2, "order after the caller's stream"};
+}
+
 // host copy of a device row pointer, checked (starts at 0, non-decreasing,
 // rows of at most max_row entries); returns nnz or -1
 int64_t checked_rowptr(const int32_t* rowptr, int64_t m, int64_t max_row) {
@@ -30,6 +41,7 @@ int64_t checked_rowptr(const int32_t* rowptr, int64_t m, int64_t max_row) {
 // copy a device CSR into a slot and build its CSC / work lists; false on bad entries
 bool load_slot(Slot& S, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* colidx,
                const float* vals) {
+  after_caller(S.stream);
   SFD_CUDA(cudaMemcpyAsync(S.csr.ptr, rowptr, (m + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
                            S.stream));
   if (nnz > 0) {
@@ -52,7 +64,7 @@ int run_dense(F&& f) {
   DevArena A;
   cudaStream_t s = nullptr;
   try {
-    SFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    SFD_CUDA(cudaStreamCreate(&s));
     Workspace ws;
     alloc_dense_scratch(A, ws);
     f(ws, s);
@@ -150,6 +162,7 @@ int sfd_dense_shrink(int64_t rows, int64_t d, int32_t ell, const float* M, float
     return SFD_EINVAL;
   try {
     Merger G(d, ell);
+    after_caller(G.stream);
     // rows 0..min(rows,l) are the "B" block, the rest the stacked block
     const int k0 = (int)std::min<int64_t>(rows, ell);
     const int k1 = (int)(rows - k0);
@@ -192,7 +205,7 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
   DevArena A;
   cudaStream_t s = nullptr;
   try {
-    SFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    SFD_CUDA(cudaStreamCreate(&s));
     Workspace ws;
     alloc_dense_scratch(A, ws);
     float* tmp = A.alloc<float>((size_t)rows * ld);
@@ -241,7 +254,7 @@ int sfd_symeig(int32_t n, const float* S, int32_t nwant, float* evals, float* ev
   DevArena A;
   cudaStream_t s = nullptr;
   try {
-    SFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    SFD_CUDA(cudaStreamCreate(&s));
     float* work = A.alloc<float>(symeig_work_floats(kMaxEig, kMaxEig));
     symeig(S, n, nwant, evals, evecs, work, s);
     SFD_CUDA(cudaStreamSynchronize(s));

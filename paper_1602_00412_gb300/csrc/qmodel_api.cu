@@ -28,7 +28,7 @@ bool all_finite(const float* p, int64_t n) {
 struct Buffers {
   DevArena A;
   cudaStream_t s = nullptr;
-  Buffers() { SFD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)); }
+  Buffers() { SFD_CUDA(cudaStreamCreate(&s)); }
   ~Buffers() {
     if (s) cudaStreamSynchronize(s);
     A.release();

@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/sfd.h).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -131,6 +132,10 @@ void build_work(Csr& c, cudaStream_t s);
 // Y[seg, 0:k] = sum over entries of seg: val * X[idx, 0:k]  (k <= 256, lds % 4 == 0)
 void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
           cudaStream_t s);
+// Same with X stored as fp16 (k <= 128, ldx % 8 == 0): the gather moves half
+// the bytes; products and sums are fp32.
+void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, float* partial,
+            cudaStream_t s);
 // y[seg] = scale_ptr? * sum val * x[idx]
 void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s);
 
@@ -164,8 +169,10 @@ void gram_reduce_tiles(const float* partial, int nchunks, int n, float* G, cudaS
 bool tc_supported(int n, int kout);
 void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
              cudaStream_t s);
+// Yh (optional): write Y as fp16 into Yh (ld ldy, a multiple of 8, >= kout;
+// columns kout..ldy-1 get 0) instead of fp32 into Y; for |entries| <= 1.
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
-                float* Y, int ldy, Workspace& ws, cudaStream_t s);
+                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh = nullptr);
 // Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
 // row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
 // clamped.

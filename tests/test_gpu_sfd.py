@@ -182,3 +182,20 @@ def test_pipeline_depth_does_not_change_the_sketch(lib):
     X = synth.c1_gapped(seed=seed, n=9000)
     outs = [_run_gpu(lib, X, d, ell, seed, slots=s)[0] for s in (1, 2, 3)]
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sketch_between_appends_changes_nothing(lib, precision):
+    # reading the sketch (host copy) between buffers must leave the stream's
+    # state alone: the same sketch as one append and one read at the end
+    d, ell, seed = 2000, 50, 6
+    X = synth.c1_gapped(seed=seed, n=8000)
+    s = lib.SFD(d, ell, seed, precision=precision, slots=1)
+    for b in range(4):
+        part = X.rows(b * d, (b + 1) * d)
+        s.append(part.indptr, part.indices, part.values)
+        Bb = s.sketch()
+        assert np.all(np.isfinite(Bb))
+    s.close()
+    B1, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, slots=1)
+    assert np.array_equal(Bb.astype(np.float64), B1)
