@@ -357,7 +357,8 @@ def ours_arm(args, rank, world, local):
            "e2e": {"value": e2e, "unit": "nnz/s",
                    "h2d_bytes_per_step": int(X.indptr.nbytes + X.indices.nbytes + X.values.nbytes),
                    "d2h_bytes_per_step": int(B_h.nbytes)},
-           "roofline": {"kernel": "k_spmm (A'X via CSR, A'^T Y via CSC, incl. split fix-up)",
+           "roofline": {"kernel": "SpMM stage: k_spmm_h (fp16 blocks) / k_spmm (fp32) for A'X (CSR) "
+                                  "and A'^T Y (CSC), incl. split fix-up",
                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": (achieved / peak) if achieved else None,
                         "peak_kind": "of %s" % peak_kind,

@@ -119,13 +119,15 @@ __device__ __forceinline__ void cp_async_wait() {
 // partial[chunk] (128 x 128 row-major; only the leading n x n block is
 // written) = X[rows of chunk, 0:n]^T X[rows of chunk, 0:n]. Rows are staged
 // 32 at a time (K = 32: four MMAs) through a ring of kGSt buffers filled by
-// cp.async, kGSt - 1 stages ahead of the MMAs; a buffer is refilled once the
-// MMAs that read it have completed (its mbarrier). Element (m, k) of a stage
-// is X[row k][column m], four consecutive rows per 16-byte core row.
+// cp.async kGLook stages ahead of the MMAs. A buffer is refilled once the MMAs
+// that read it have completed (its mbarrier); those were issued two stages
+// earlier, so the wait rarely blocks. Element (m, k) of a stage is
+// X[row k][column m], four consecutive rows per 16-byte core row.
 constexpr int kGK = 32;             // rows per stage
 constexpr int kGTile = 128 * kGK;   // floats per stage
-constexpr int kGSt = 4;             // stages in the ring
-constexpr int kGramSmem = kGSt * kGTile * (int)sizeof(float);  // 64 KB: <= 3 CTAs per SM
+constexpr int kGSt = 6;             // stages in the ring
+constexpr int kGLook = kGSt - 2;    // stages loaded ahead of the MMAs
+constexpr int kGramSmem = kGSt * kGTile * (int)sizeof(float);  // 96 KB: <= 2 CTAs per SM
 constexpr int kGramChunks = 152;
 
 __global__ void __launch_bounds__(kTcThreads)
@@ -166,12 +168,12 @@ __global__ void __launch_bounds__(kTcThreads)
   uint32_t phase_bits = 0, used_bits = 0;
   bool ok = true;
 #pragma unroll
-  for (int st = 0; st < kGSt - 1; ++st) {
+  for (int st = 0; st < kGLook; ++st) {
     if (st < nst) issue(st);
     cp_async_commit();
   }
   for (int st = 0; st < nst; ++st) {
-    const int ns = st + kGSt - 1;
+    const int ns = st + kGLook;
     if (ns < nst) {
       const int b = ns % kGSt;
       if (used_bits & (1u << b)) {  // the MMAs that read this buffer must be done
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads)
       issue(ns);
     }
     cp_async_commit();
-    cp_async_wait<kGSt - 1>();  // this thread's copies of stage st have landed
+    cp_async_wait<kGLook>();  // this thread's copies of stage st have landed
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
     const int b = st % kGSt;

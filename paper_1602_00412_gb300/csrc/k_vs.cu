@@ -137,15 +137,15 @@ __global__ void __launch_bounds__(256)
 }
 
 // v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block
-// (fixed grid). A warp reads a row as float4 lanes and takes four rows at a
-// time (independent loads in flight); lane 0 keeps the block's rows' squares
-// in row order.
+// (fixed grid). A warp takes four rows at a time: their float4 row pieces and
+// the four v entries are loaded before any arithmetic, so the loads overlap;
+// lane 0 keeps the block's squares in row order.
 __global__ void __launch_bounds__(256)
     k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
                const float* __restrict__ w, float* __restrict__ part) {
   __shared__ float4 ws[kMaxEll / 4];
   __shared__ float red[8];
-  const int nvec = (ell + 3) >> 2;
+  const int nvec = (ell + 3) >> 2;  // <= 64
   for (int c = threadIdx.x; c < kMaxEll / 4; c += blockDim.x) {
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
     if (4 * c + 0 < ell) t.x = w[4 * c + 0];
@@ -159,26 +159,38 @@ __global__ void __launch_bounds__(256)
   const float4* B4 = reinterpret_cast<const float4*>(Bt);
   const int ld4 = ld >> 2;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const float4 q0 = lane < nvec ? ws[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 q1 = lane + 32 < nvec ? ws[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float acc2 = 0.f;
   for (int64_t j = ((int64_t)blockIdx.x * 8 + wp) * 4; j < d; j += nwarps * 4) {
+    float4 b0[4], b1[4];
+    float vv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const bool row = j + r < d;
+      b0[r] = row && lane < nvec ? B4[(j + r) * ld4 + lane] : z4;
+      b1[r] = row && lane + 32 < nvec ? B4[(j + r) * ld4 + lane + 32] : z4;
+      vv[r] = row && lane == 0 ? v[j + r] : 0.f;
+    }
     float s[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      float t = 0.f;
-      if (j + r < d)
-        for (int c4 = lane; c4 < nvec; c4 += 32) {
-          const float4 b = B4[(j + r) * ld4 + c4], q = ws[c4];
-          t = fmaf(b.x, q.x, fmaf(b.y, q.y, fmaf(b.z, q.z, fmaf(b.w, q.w, t))));
-        }
-      s[r] = t;
+      float t = b0[r].x * q0.x;
+      t = fmaf(b0[r].y, q0.y, t);
+      t = fmaf(b0[r].z, q0.z, t);
+      t = fmaf(b0[r].w, q0.w, t);
+      t = fmaf(b1[r].x, q1.x, t);
+      t = fmaf(b1[r].y, q1.y, t);
+      t = fmaf(b1[r].z, q1.z, t);
+      t = fmaf(b1[r].w, q1.w, t);
+      s[r] = warp_sum(t);
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) s[r] = warp_sum(s[r]);
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (j + r < d) {
-          const float nv = v[j + r] - s[r];
+          const float nv = vv[r] - s[r];
           v[j + r] = nv;
           acc2 = fmaf(nv, nv, acc2);
         }
