@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SFD_ABI_VERSION 2u
+#define SFD_ABI_VERSION 3u
 
 #define SFD_OK 0
 #define SFD_EINVAL 1   /* bad argument: l < 1, l > d, index outside [0,d), non-monotone indptr, NaN/Inf value, ... */
@@ -80,6 +80,9 @@ typedef struct sfd_options {
                            {1,2,3,4,6,8,11,16,23,32,45,64} below q_fixed whose attempt passes
                            VerifySpectral and keeps ||P||_F^2 >= (1 - q_tau) times its value at
                            q_fixed (same G); q_fixed if none does (default 1e-2) */
+  int32_t autotune;     /* 1 (default): each slot times the unroll variants of its sparse
+                           products on first use and keeps the fastest per pass (the variants
+                           give identical results); 0: the default variant */
 } sfd_options;
 
 /* Counters of a context (Alg. 2 / Alg. 4 bookkeeping). */

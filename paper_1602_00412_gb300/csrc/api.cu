@@ -315,6 +315,7 @@ void sfd_options_init(sfd_options* o) {
   o->retry_cap = 8;
   o->q_margin = 1.0f;
   o->q_tau = 1e-2f;
+  o->autotune = 1;
 }
 
 const char* sfd_strerror(int s) {
@@ -368,6 +369,7 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
         C.slots.emplace_back(new Slot(d, ell, d, cap_nnz, nullptr));
         C.slots.back()->profile = C.opt.profile != 0;
         C.slots.back()->mixed = C.opt.precision == 1;
+        C.slots.back()->autotune = C.opt.autotune != 0;
       } catch (const CudaError& e) {
         // fewer slots when memory is short; at least one is required
         if (e.err != cudaErrorMemoryAllocation || C.slots.empty()) throw;

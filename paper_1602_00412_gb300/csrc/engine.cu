@@ -127,6 +127,12 @@ Slot::~Slot() { cleanup(); }
 void Slot::cleanup() {
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   ev_pool.clear();
+  for (cudaEvent_t& e : tune_ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  vs_graphs.release();
   arena.release();
   if (verdict_host) cudaFreeHost(verdict_host);
   if (ptr_host) cudaFreeHost(ptr_host);
@@ -178,10 +184,42 @@ bool Slot::orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half*
   return tc && Xh;
 }
 
+// Time every unroll variant of this pass once (after one warm-up launch each)
+// and keep the fastest. The variants give identical results, so tuning never
+// changes the sketch; it costs one host wait per variant on a slot's first
+// products.
+int Slot::tune_spmm(const Csr& c, const float* X, const __half* Xh, float* Yo) {
+  if (!tune_ev[0]) {
+    SFD_CUDA(cudaEventCreate(&tune_ev[0]));
+    SFD_CUDA(cudaEventCreate(&tune_ev[1]));
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < spmm_variants(Xh != nullptr); ++v) {
+    for (int rep = 0; rep < 2; ++rep) {
+      SFD_CUDA(cudaEventRecord(tune_ev[0], stream));
+      if (Xh) spmm_h(c, Xh, ld, ld, Yo, ld, ws.partial_rows, stream, v);
+      else spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream, v);
+      SFD_CUDA(cudaEventRecord(tune_ev[1], stream));
+    }
+    SFD_CUDA(cudaEventSynchronize(tune_ev[1]));
+    float ms = 0.f;
+    SFD_CUDA(cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]));
+    if (v == 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  return best;
+}
+
 void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in, const __half* Xh) {
+  int& choice = spmm_choice[&c == &csc ? 1 : 0][Xh ? 1 : 0];
+  if (choice < 0) choice = autotune ? tune_spmm(c, X, Xh, Yo) : 0;
+  const int variant = choice;
   auto run = [&] {
-    if (Xh) spmm_h(c, Xh, ld, ld, Yo, ld, ws.partial_rows, stream);
-    else spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream);
+    if (Xh) spmm_h(c, Xh, ld, ld, Yo, ld, ws.partial_rows, stream, variant);
+    else spmm(c, X, ld, ld, Yo, ld, ws.partial_rows, stream, variant);
   };
   if (!profile) {
     run();
@@ -269,7 +307,7 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
   launch_delta(fro2, ws.scalars, ell, stream);
   if (verify) {
     VsArgs a{&csr, &csc, Bpt, ld, ell, d, m, ws.scalars + kSscale, p, seed, b, r};
-    verify_spectral(a, ws, stream);
+    verify_spectral(a, ws, stream, &vs_graphs);
   }
   launch_verdict(fro2, ws.scalars, ws.flags, ws.evals, ell, verify, verdict_dev, stream);
   SFD_CUDA(cudaMemcpyAsync(verdict_host, verdict_dev, sizeof(Verdict), cudaMemcpyDeviceToHost,

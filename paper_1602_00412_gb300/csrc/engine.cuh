@@ -81,6 +81,12 @@ struct Slot {
   // precision 1: the orthonormalisations inside the power iterations run their
   // Gram and X R^-1 on tensor cores (TF32 inputs, FP32 accumulate)
   bool mixed = false;
+  // autotuning of the sparse products: the unroll variant of each pass
+  // ([A' X (CSR), A'^T Y (CSC)] x [fp32, fp16 X]), timed on its first use
+  bool autotune = false;
+  int spmm_choice[2][2] = {{-1, -1}, {-1, -1}};
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  VsGraphs vs_graphs;  // VerifySpectral steps, captured on first use
   // profiling of the sparse products
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -114,6 +120,7 @@ struct Slot {
   bool orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half* Xh = nullptr);
   void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in,
                   const __half* Xh = nullptr);
+  int tune_spmm(const Csr& c, const float* X, const __half* Xh, float* Yo);
 };
 
 struct Merger {

@@ -589,18 +589,28 @@ void build_work(Csr& c, cudaStream_t s) {
 }
 
 void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
-          cudaStream_t s) {
+          cudaStream_t s, int variant) {
   const SegWork& w = c.work;
   const int nvec = (k + 3) / 4;
   const int grid = (w.cap_items + 7) / 8;
-  if (nvec <= 32)
-    k_spmm<1, 8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
-                                      (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                      (float4*)partial);
-  else
-    k_spmm<2, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
-                                      (const float4*)X, ldx / 4, nvec, (float4*)Y, ldy / 4,
-                                      (float4*)partial);
+  const float4* X4 = (const float4*)X;
+  float4* Y4 = (float4*)Y;
+  float4* P4 = (float4*)partial;
+  if (nvec <= 32) {
+    if (variant == 1)
+      k_spmm<1, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                        X4, ldx / 4, nvec, Y4, ldy / 4, P4);
+    else
+      k_spmm<1, 8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                        X4, ldx / 4, nvec, Y4, ldy / 4, P4);
+  } else {
+    if (variant == 1)
+      k_spmm<2, 2><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                        X4, ldx / 4, nvec, Y4, ldy / 4, P4);
+    else
+      k_spmm<2, 4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
+                                        X4, ldx / 4, nvec, Y4, ldy / 4, P4);
+  }
   SFD_LAUNCH_CHECK();
   const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));
   if (nvec <= 32)
@@ -615,15 +625,22 @@ void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float
 }
 
 void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, float* partial,
-            cudaStream_t s) {
+            cudaStream_t s, int variant) {
   if (k > 128 || (ldx & 7) || (ldy & 7))
     throw CudaError{cudaErrorInvalidValue, "spmm_h: k <= 128, ldx and ldy multiples of 8"};
   const SegWork& w = c.work;
   const int nv8 = (k + 7) / 8;
   const int grid = (w.cap_items + 7) / 8;
-  k_spmm_h<4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items,
-                                   reinterpret_cast<const uint4*>(X), ldx / 8, nv8, (float4*)Y,
-                                   ldy / 4, (float4*)partial);
+  const uint4* X8 = reinterpret_cast<const uint4*>(X);
+  if (variant == 1)
+    k_spmm_h<2><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items, X8,
+                                     ldx / 8, nv8, (float4*)Y, ldy / 4, (float4*)partial);
+  else if (variant == 2)
+    k_spmm_h<8><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items, X8,
+                                     ldx / 8, nv8, (float4*)Y, ldy / 4, (float4*)partial);
+  else
+    k_spmm_h<4><<<grid, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot, w.d_n_items, X8,
+                                     ldx / 8, nv8, (float4*)Y, ldy / 4, (float4*)partial);
   SFD_LAUNCH_CHECK();
   const int nvec = 2 * nv8;  // float4 columns written per row
   const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));

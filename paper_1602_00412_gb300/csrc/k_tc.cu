@@ -202,9 +202,14 @@ __global__ void __launch_bounds__(kTcThreads)
     used_bits |= 1u << b;
   }
   cp_async_wait<0>();
-  if (ok && nst > 0) {  // MMAs complete in order: the last commit covers all
-    const int b = (nst - 1) % kGSt;
-    ok = __syncthreads_and(mbar_wait(&mbar[b], (phase_bits >> b) & 1u));
+  if (ok) {
+    // every commit not yet waited for (one per buffer in use), so that no
+    // mbarrier arrival can land after the CTA has released its shared memory
+    bool all = true;
+    for (int b = 0; b < kGSt; ++b)
+      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u) && all;
+    ok = __syncthreads_and(all);
+    if (ok) used_bits = 0;
   }
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);

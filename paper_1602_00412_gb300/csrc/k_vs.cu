@@ -245,7 +245,51 @@ void launch_verdict(const double* fro2a, const double* scal, const int* flags,
   SFD_LAUNCH_CHECK();
 }
 
-void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
+namespace {
+
+// One power step x -> v (u = A'x, w = B'x, v = A'^T u - B'^T w, log ||v||,
+// v /= ||v||); the caller swaps x and v.
+void vs_step(const VsArgs& a, Workspace& ws, float* x, float* u, float* v, float* w, float* part,
+             double* scal, cudaStream_t s) {
+  spmv(*a.csr, x, u, ws.partial_rows, s);
+  k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, ws.wpart);
+  SFD_LAUNCH_CHECK();
+  k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
+  SFD_LAUNCH_CHECK();
+  spmv(*a.csc, u, v, ws.partial_rows, s);
+  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
+  SFD_LAUNCH_CHECK();
+  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale_dev, 1, scal);
+  SFD_LAUNCH_CHECK();
+  k_scale<<<kVsBlocks, 256, 0, s>>>(v, a.d, scal);
+  SFD_LAUNCH_CHECK();
+}
+
+// Capture `steps` power steps; *nodes = the kernels in the graph. The launches
+// made while capturing are taken off the launch counter again: the kernels
+// run when the graph is replayed, and each replay is counted then.
+cudaGraphExec_t capture(cudaStream_t s, int steps, const VsArgs& a, Workspace& ws, float* x,
+                        float* u, float* v, float* w, float* part, double* scal, size_t* nodes) {
+  SFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int t = 0; t < steps; ++t) {
+    vs_step(a, ws, x, u, v, w, part, scal, s);
+    std::swap(x, v);
+  }
+  cudaGraph_t g = nullptr;
+  SFD_CUDA(cudaStreamEndCapture(s, &g));
+  *nodes = 0;
+  cudaGraphGetNodes(g, nullptr, nodes);
+  __atomic_sub_fetch(&g_kernel_launches, (unsigned long long)*nodes, __ATOMIC_RELAXED);
+  cudaGraphExec_t e = nullptr;
+  const cudaError_t rc = cudaGraphInstantiate(&e, g, 0);
+  cudaGraphDestroy(g);
+  if (rc != cudaSuccess) throw CudaError{rc, "cudaGraphInstantiate"};
+  return e;
+}
+
+}  // namespace
+
+void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s, VsGraphs* graphs) {
   float* x = ws.vec0;   // d
   float* u = ws.vec1;   // m
   float* v = ws.vec2;   // d
@@ -260,21 +304,24 @@ void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s) {
   SFD_LAUNCH_CHECK();
   k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
   SFD_LAUNCH_CHECK();
-  for (int t = 0; t < a.p; ++t) {
-    spmv(*a.csr, x, u, ws.partial_rows, s);
-    k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, ws.wpart);
-    SFD_LAUNCH_CHECK();
-    k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
-    SFD_LAUNCH_CHECK();
-    spmv(*a.csc, u, v, ws.partial_rows, s);
-    k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
-    SFD_LAUNCH_CHECK();
-    k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale_dev, 1, scal);
-    SFD_LAUNCH_CHECK();
-    std::swap(x, v);
-    k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
-    SFD_LAUNCH_CHECK();
+  if (!graphs) {
+    for (int t = 0; t < a.p; ++t) {
+      vs_step(a, ws, x, u, v, w, part, scal, s);
+      std::swap(x, v);
+    }
+    return;
   }
+  if (!graphs->one) {
+    size_t n1 = 0, n2 = 0;
+    graphs->one = capture(s, 1, a, ws, x, u, v, w, part, scal, &n1);
+    graphs->two = capture(s, 2, a, ws, x, u, v, w, part, scal, &n2);
+    graphs->kernels_per_step = (int)n1;
+  }
+  // x starts in vec0 and is back there after every two steps
+  for (int t = 0; t + 1 < a.p; t += 2) SFD_CUDA(cudaGraphLaunch(graphs->two, s));
+  if (a.p & 1) SFD_CUDA(cudaGraphLaunch(graphs->one, s));
+  __atomic_add_fetch(&g_kernel_launches, (unsigned long long)graphs->kernels_per_step * a.p,
+                     __ATOMIC_RELAXED);
 }
 
 }  // namespace sfd

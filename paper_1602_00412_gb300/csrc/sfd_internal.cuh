@@ -130,12 +130,16 @@ void radix_sort_by_key(int* key, int* a, float* b, int* key_alt, int* a_alt, flo
 // Work list of a segmented structure (split segments longer than kSplit).
 void build_work(Csr& c, cudaStream_t s);
 // Y[seg, 0:k] = sum over entries of seg: val * X[idx, 0:k]  (k <= 256, lds % 4 == 0)
+// variant: how many gathers each lane keeps in flight (0: the default; the
+// variants differ only in unrolling, never in results; spmm_variants(true)
+// tells how many the fp16 form has)
 void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,
-          cudaStream_t s);
+          cudaStream_t s, int variant = 0);
+inline int spmm_variants(bool half) { return half ? 3 : 2; }
 // Same with X stored as fp16 (k <= 128, ldx % 8 == 0): the gather moves half
 // the bytes; products and sums are fp32.
 void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, float* partial,
-            cudaStream_t s);
+            cudaStream_t s, int variant = 0);
 // y[seg] = scale_ptr? * sum val * x[idx]
 void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s);
 
@@ -210,9 +214,22 @@ struct VsArgs {
   int p;
   uint64_t seed, b, r;
 };
+// CUDA graphs of one and of two power steps (the step's arguments are fixed
+// for the workspace and the CSR/CSC copies it is used with), captured on first
+// use and replayed; owned by the caller.
+struct VsGraphs {
+  cudaGraphExec_t one = nullptr, two = nullptr;
+  int kernels_per_step = 0;
+  void release() {
+    if (one) cudaGraphExecDestroy(one);
+    if (two) cudaGraphExecDestroy(two);
+    one = two = nullptr;
+  }
+};
 // Enqueues p power steps; log ||C^p x|| lands in ws.scalars[kSlogsum],
 // ws.scalars[kSzero] = 1 if some C x_t vanished. No host synchronisation.
-void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s);
+// With graphs (not null) the steps are replayed from its CUDA graphs.
+void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s, VsGraphs* graphs = nullptr);
 
 // Device scalars of one SparseShrink attempt (ws.scalars[...]).
 enum : int {

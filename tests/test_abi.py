@@ -43,7 +43,7 @@ def test_options_defaults(lib):
     assert (o.delta, o.verify, o.c_q, o.q_override, o.retry_cap) == (0.01, 1, 0.25, -1, 8)
     assert o.cuda_stream is None
     assert (o.precision, o.q_mode, o.slots) == (0, 0, 0)
-    assert o.q_margin == 1.0 and abs(o.q_tau - 1e-2) < 1e-9
+    assert o.q_margin == 1.0 and abs(o.q_tau - 1e-2) < 1e-9 and o.autotune == 1
 
 
 def test_create_rejects_bad_shapes_without_gpu(lib):

@@ -199,3 +199,13 @@ def test_sketch_between_appends_changes_nothing(lib, precision):
     s.close()
     B1, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, slots=1)
     assert np.array_equal(Bb.astype(np.float64), B1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuning_never_changes_the_sketch(lib, precision):
+    # the tuned unroll variants of the sparse products give identical results
+    d, ell, seed = 2000, 50, 8
+    X = synth.c1_gapped(seed=seed, n=6000)
+    Bt, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, autotune=1)
+    Bn, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, autotune=0)
+    assert np.array_equal(Bt, Bn)
