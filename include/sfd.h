@@ -62,7 +62,10 @@ typedef struct sfd_options {
   int32_t precision;    /* 0: plain fp32 (default); 1: mixed: for l <= 128 the orthonormalisations
                            of every power iteration of Alg. 1 but the last form their Gram and
                            X R^-1 on tcgen05 tensor cores (TF32 inputs, FP32 accumulation);
-                           every other stage stays FP32 */
+                           the other dense products (last iteration, second CholeskyQR pass,
+                           P P^T and B'^T of Alg. 3) keep FP32 accuracy: tensor cores in the
+                           split form of sfd_gram (precision 2) where l allows, else CUDA
+                           cores; the sparse products and eigensolvers stay FP32 */
   int32_t q_mode;       /* power count per buffer. 0: the fixed schedule (default); 1: learned:
                            q = clamp(ceil(network(features) + q_margin), 1, q_fixed) with the
                            network set by sfd_set_q_model (fixed schedule until one is set); a
@@ -277,7 +280,11 @@ int sfd_q_train(int64_t n, const float* features, const float* targets, int32_t 
  * be 0 (G = 0, Y untouched). precision 0: FP32 on the CUDA cores, sums in a
  * fixed order (bit-reproducible); precision 1: tcgen05 tensor cores, inputs
  * rounded to TF32 (10-bit mantissa), FP32 accumulation, for k, n, kout <= 128
- * (larger returns SFD_EINVAL). Errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA,
+ * (larger returns SFD_EINVAL); precision 2: tensor cores in the split form
+ * (each input x = x_hi + x_lo, x_hi = x with its 13 low mantissa bits
+ * cleared; x_hi y_hi + x_hi y_lo + x_lo y_hi accumulated in FP32: about 21
+ * significant bits), for k <= 128 in sfd_gram and n, kout <= 112 in
+ * sfd_gemm_ts (larger returns SFD_EINVAL). Errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA,
  * SFD_ETIMEOUT (a bounded tensor-core wait ran out; the outputs are not valid). */
 int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int32_t precision);
 int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const float* T, int32_t kout,

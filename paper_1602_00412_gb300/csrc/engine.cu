@@ -173,15 +173,18 @@ void Slot::build(int m, int64_t nnz) {
   build_work(csc, stream);
 }
 
-bool Slot::orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half* Xh) {
+bool Slot::orth_pass(const float* X, int64_t rows, float* Xout, int form, __half* Xh) {
   const ColMap map = single_map(ell);
-  tc = tc && tc_supported(ell, ell);
-  if (tc) gram_tc(X, ld, map, rows, ws.small_a, ws, stream);
+  if (!tc_supported(ell, ell)) form = 0;
+  const bool split = form == 2;
+  if (form) gram_tc(X, ld, map, rows, ws.small_a, ws, stream, split);
   else gram(X, ld, map, rows, ws.small_a, ws, stream);
   chol_inv(ws.small_a, ell, ws.small_b, ws.eig_work, ws.flags, stream);
-  if (tc) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, Xh);
+  if (form == 1) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, Xh);
+  else if (split && tc_split_supported(ell, ell))
+    gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, nullptr, true);
   else gemm_ts(X, ld, map, rows, ws.small_b, ell, Xout, ld, stream);
-  return tc && Xh;
+  return form == 1 && Xh;
 }
 
 // Time every unroll variant of this pass once (after one warm-up launch each)
@@ -261,15 +264,19 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
   // Alg. 1: G ~ N(0,1)^{d x l}; Y = orth(A' G); q x { W = orth(A'^T Y); Y = orth(A' W) }
   launch_gauss_fill(W, d, ell, ld, seed, b, r, 1, stream);
   // mixed precision: the orthonormalisations of every power iteration but the
-  // last run on tensor cores; the last iteration and the second CholeskyQR
-  // pass on Z stay FP32, so the TF32 perturbation of the subspace is damped by
-  // one more FP32 iteration and Z is orthonormal to FP32 accuracy
-  // Mixed precision also stores the orthonormal blocks between a tensor-core
+  // last run on tensor cores in TF32 (form 1); the last iteration, the second
+  // CholeskyQR pass on Z and the products of Alg. 3 keep FP32 accuracy, so the
+  // TF32 perturbation of the subspace is damped by one more accurate iteration
+  // and Z is orthonormal to FP32 accuracy. Those accurate stages run on tensor
+  // cores as well, in the split form (form 2: hi and lo TF32 parts, three
+  // MMAs, ~21 significant bits), where l allows; else on the CUDA cores.
+  // Mixed precision also stores the orthonormal blocks between a TF32
   // orthonormalisation and the next sparse product as fp16 (|entries| <= 1,
   // the TF32 inputs' precision), so the product's gather moves half the bytes.
+  const int exact_form = mixed ? 2 : 0;
   spmm_timed(csr, W, Y, d);
   // leaves S0 = (A'G)^T (A'G) in ws.small_a
-  bool y_half = orth_pass(Y, m, Y2, mixed && q > 0, Yh);
+  bool y_half = orth_pass(Y, m, Y2, mixed ? (q > 0 ? 1 : 2) : 0, Yh);
   if (!y_half) std::swap(Y, Y2);
   if (qc && (qc->predict || qc->features)) {
     q_features(csr, csc, d, ell, qc->q_fixed, fro2, ws.small_a, qfeat, qacc, stream);
@@ -283,7 +290,7 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
     }
   }
   for (int t = 0; t < q; ++t) {
-    const bool tc = mixed && t + 1 < q;
+    const int tc = t + 1 < q && mixed ? 1 : exact_form;
     spmm_timed(csc, Y, W, m, y_half ? Yh : nullptr);
     const bool w_half = orth_pass(W, d, W2, tc, Wh);
     if (!w_half) std::swap(W, W2);
@@ -293,16 +300,19 @@ int Slot::enqueue_attempt(int m, int q, uint64_t seed, uint64_t b, uint64_t r, i
   }
   // here Y is fp32: a tensor-core first pass implies q >= 1 (the predicted q
   // is at least 1 as well), and the last iteration is fp32
-  orth_pass(Y, m, Y2, false);  // second CholeskyQR pass on Z
+  orth_pass(Y, m, Y2, exact_form);  // second CholeskyQR pass on Z
   std::swap(Y, Y2);
   // Alg. 3: P^T = A'^T Z, svd(P, l) through P P^T, B'^T = P^T H diag(s)
   spmm_timed(csc, Y, W, m);
   const ColMap map = single_map(ell);
-  gram(W, ld, map, d, ws.small_a, ws, stream);
+  if (mixed && tc_supported(ell, ell)) gram_tc(W, ld, map, d, ws.small_a, ws, stream, true);
+  else gram(W, ld, map, d, ws.small_a, ws, stream);
   symeig(ws.small_a, ell, ell, ws.evals, ws.small_b, ws.eig_work, stream, true);
   shrink_weights(ws.evals, ws.small_b, ell, ell, ell, 0, ws.small_a, ws.scalars, stream);
   wait_freed();  // DenseShrink of this slot's previous buffer must have read B'^T
-  gemm_ts(W, ld, map, d, ws.small_a, ell, Bpt, ld, stream);
+  if (mixed && tc_split_supported(ell, ell))
+    gemm_ts_tc(W, ld, map, d, ws.small_a, ell, Bpt, ld, ws, stream, nullptr, true);
+  else gemm_ts(W, ld, map, d, ws.small_a, ell, Bpt, ld, stream);
   // Alg. 4: Delta; Alg. 6: VerifySpectral
   launch_delta(fro2, ws.scalars, ell, stream);
   if (verify) {

@@ -79,7 +79,8 @@ struct Slot {
   int* q_host = nullptr;            // pinned, 1
   int* ptr_host = nullptr;          // pinned staging of the local row pointer
   // precision 1: the orthonormalisations inside the power iterations run their
-  // Gram and X R^-1 on tensor cores (TF32 inputs, FP32 accumulate)
+  // Gram and X R^-1 on tensor cores (TF32 inputs, FP32 accumulate), the
+  // accurate stages in the split TF32 form
   bool mixed = false;
   // autotuning of the sparse products: the unroll variant of each pass
   // ([A' X (CSR), A'^T Y (CSC)] x [fp32, fp16 X]), timed on its first use
@@ -115,9 +116,11 @@ struct Slot {
 
  private:
   void cleanup();
-  // CholeskyQR step X -> Xout; with tc and Xh, the result goes to Xh as fp16
-  // only (returns true then)
-  bool orth_pass(const float* X, int64_t rows, float* Xout, bool tc, __half* Xh = nullptr);
+  // CholeskyQR step X -> Xout. form 0: CUDA cores, FP32; 1: tensor cores,
+  // TF32 inputs; 2: tensor cores, split TF32 (FP32-accurate). Forms 1 and 2
+  // need l <= 128 (else form 0 runs). With form 1 and Xh, the result goes to
+  // Xh as fp16 only (returns true then).
+  bool orth_pass(const float* X, int64_t rows, float* Xout, int form, __half* Xh = nullptr);
   void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in,
                   const __half* Xh = nullptr);
   int tune_spmm(const Csr& c, const float* X, const __half* Xh, float* Yo);

@@ -125,14 +125,28 @@ __device__ __forceinline__ void cp_async_wait() {
 // X[row k][column m], four consecutive rows per 16-byte core row.
 constexpr int kGK = 32;             // rows per stage
 constexpr int kGTile = 128 * kGK;   // floats per stage
-constexpr int kGSt = 6;             // stages in the ring
-constexpr int kGLook = kGSt - 2;    // stages loaded ahead of the MMAs
-constexpr int kGramSmem = kGSt * kGTile * (int)sizeof(float);  // 96 KB: <= 2 CTAs per SM
 constexpr int kGramChunks = 152;
+// SPLIT (the fp32-accurate form): every value x is split into x_hi (x with
+// the 13 low mantissa bits cleared, exactly a TF32 number) and x_lo = x - x_hi
+// (exact in fp32), and X^T X is accumulated as hi^T hi + hi^T lo + lo^T hi:
+// about 21 significant bits instead of TF32's 11.
+template <bool SPLIT>
+struct GramRing {
+  static constexpr int St = SPLIT ? 4 : 6;  // stages in the ring
+  static constexpr int Look = St - 2;       // stages loaded ahead of the MMAs
+  static constexpr int Smem = St * kGTile * (SPLIT ? 2 : 1) * (int)sizeof(float);  // 128 / 96 KB
+};
 
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_gram(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_chunk,
               float* __restrict__ partial, int* __restrict__ flags) {
+  constexpr int kGSt = GramRing<SPLIT>::St;
+  constexpr int kGLook = GramRing<SPLIT>::Look;
   extern __shared__ __align__(1024) float smem[];
   __shared__ __align__(8) uint64_t mbar[kGSt];
   __shared__ uint32_t tmem_slot;
@@ -152,6 +166,7 @@ __global__ void __launch_bounds__(kTcThreads)
   const int64_t r_end = min(rows, r_beg + rows_per_chunk);
   const int nst = r_end > r_beg ? (int)((r_end - r_beg + kGK - 1) / kGK) : 0;
   const uint32_t sbase = smem_u32(smem);
+  const uint32_t lo_base = sbase + (uint32_t)(kGSt * kGTile) * 4u;  // SPLIT: the lo ring
   // thread tid copies column m = tid of the 32 rows of a stage
   const int m = tid;
   auto issue = [&](int st) {
@@ -186,16 +201,35 @@ __global__ void __launch_bounds__(kTcThreads)
     }
     cp_async_commit();
     cp_async_wait<kGLook>();  // this thread's copies of stage st have landed
+    const int b = st % kGSt;
+    if (SPLIT) {  // split the elements this thread copied: hi in place, lo in the lo ring
+      // (four consecutive k of a column are one 16-byte core row: float4)
+      float* hi = smem + b * kGTile;
+      float* lo = smem + (kGSt + b) * kGTile;
+#pragma unroll
+      for (int k = 0; k < kGK; k += 4) {
+        const int o = core_off(m, k, kGK);
+        const float4 x = *reinterpret_cast<const float4*>(hi + o);
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(hi + o) = h;
+        *reinterpret_cast<float4*>(lo + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
-    const int b = st % kGSt;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::);
       const uint32_t base = sbase + (uint32_t)(b * kGTile) * 4u;
+      const uint32_t lbase = lo_base + (uint32_t)(b * kGTile) * 4u;
 #pragma unroll
       for (int kk = 0; kk < kGK / 8; ++kk) {
         const uint64_t da = smem_desc(base + kk * 256, 128, kGK * 32);
         mma_tf32(tmem, da, da, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          const uint64_t dl = smem_desc(lbase + kk * 256, 128, kGK * 32);
+          mma_tf32(tmem, da, dl, idesc, 1u);
+          mma_tf32(tmem, dl, da, idesc, 1u);
+        }
       }
       mma_commit(&mbar[b]);
     }
@@ -374,12 +408,160 @@ __global__ void __launch_bounds__(kTcThreads)
   if (warp == 0) tmem_free(tmem, 128);
 }
 
+// Y[rows, 0:kout] = X[rows, 0:n] T in the split form: X and T^T are split
+// into TF32 hi and lo parts in shared memory and Y accumulates
+// X_hi T_hi + X_hi T_lo + X_lo T_hi (about 21 significant bits). One A tile
+// in flight (hi and lo of both operands take the shared memory); each thread
+// splits the elements it copied itself.
+template <bool VEC>
+__global__ void __launch_bounds__(kTcThreads)
+    k_tc_gemm3(const float* __restrict__ X, int ldx, int n, int64_t rows,
+               const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
+               int ldy, int* __restrict__ flags) {
+  extern __shared__ __align__(1024) float smem[];
+  float* Bh = smem;                  // Np x Kp
+  float* Bl = Bh + Np * Kp;          // Np x Kp
+  float* Ah = Bl + Np * Kp;          // 128 x Kp
+  float* Al = Ah + 128 * Kp;         // 128 x Kp
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kc_n = Kp >> 2;
+  if (warp == 0) tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  for (int i = tid; i < Np * Kp; i += kTcThreads) {  // B(j, k) = T[k][j]
+    const int j = i % Np, k = i / Np;
+    const bool ok = k < n && j < kout;
+    cp_async4(smem_u32(Bh) + (uint32_t)core_off(j, k, Kp) * 4u,
+              ok ? (const void*)(T + (int64_t)k * kout + j) : T, ok ? 4u : 0u);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  for (int i = tid; i < Np * Kp; i += kTcThreads) {
+    const int o = core_off(i % Np, i / Np, Kp);
+    const float x = Bh[o], h = tf32_hi(x);
+    Bh[o] = h;
+    Bl[o] = x - h;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, Np);
+  const int64_t ntiles = (rows + 127) / 128;
+  const bool vec_out = (ldy & 3) == 0 && ((uintptr_t)Y & 15) == 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row0 = t * 128;
+    if (VEC) {
+      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
+        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
+        const int64_t g = row0 + r;
+        const int k = kc * 4;
+        const int nval = g < rows ? max(0, min(4, n - k)) : 0;
+        cp_async16(smem_u32(Ah) + (uint32_t)core_off(r, k, Kp) * 4u,
+                   nval > 0 ? (const void*)(X + g * ldx + k) : X, (uint32_t)nval * 4u);
+      }
+    } else {
+      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
+        const int r = i / Kp, k = i % Kp;
+        const int64_t g = row0 + r;
+        const bool okk = g < rows && k < n;
+        cp_async4(smem_u32(Ah) + (uint32_t)core_off(r, k, Kp) * 4u,
+                  okk ? (const void*)(X + g * ldx + k) : X, okk ? 4u : 0u);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    if (VEC) {
+      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
+        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
+        const int o = core_off(r, kc * 4, Kp);
+        const float4 x = *reinterpret_cast<const float4*>(Ah + o);
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(Ah + o) = h;
+        *reinterpret_cast<float4*>(Al + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+    } else {
+      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
+        const int o = core_off(i / Kp, i % Kp, Kp);
+        const float x = Ah[o], h = tf32_hi(x);
+        Ah[o] = h;
+        Al[o] = x - h;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::);
+      const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
+      for (int kk = 0; kk < Kp / 8; ++kk) {
+        const uint64_t dah = smem_desc(ah + kk * 256, 128, Kp * 32);
+        const uint64_t dal = smem_desc(al + kk * 256, 128, Kp * 32);
+        const uint64_t dbh = smem_desc(bh + kk * 256, 128, Kp * 32);
+        const uint64_t dbl = smem_desc(bl + kk * 256, 128, Kp * 32);
+        mma_tf32(tmem, dah, dbh, idesc, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem, dah, dbl, idesc, 1u);
+        mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(&mbar);
+    }
+    if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::);
+    const int r = warp * 32 + lane;
+    const int64_t g = row0 + r;
+    for (int c0 = 0; c0 < Np; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (g < rows) {
+        float* y = Y + g * ldy + c0;
+        if (vec_out && c0 + 16 <= kout) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(&y[j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < kout) y[j] = v[j];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::);
+    __syncthreads();  // tensor memory and the A tile are free for the next tile
+  }
+  cp_async_wait<0>();
+  if (!ok) {
+    if (tid == 0) atomicOr(&flags[2], 1);
+    mbar_wait(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 128);
+}
+
 }  // namespace
 
 bool tc_supported(int n, int kout) { return n >= 1 && n <= 128 && kout >= 1 && kout <= 128; }
 
+static size_t gemm3_smem(int n, int kout) {
+  const int Kp = (n + 7) & ~7, Np = (kout + 15) & ~15;
+  return (size_t)2 * (Np + 128) * Kp * sizeof(float);
+}
+
+bool tc_split_supported(int n, int kout) {
+  return tc_supported(n, kout) && gemm3_smem(n, kout) <= 220 * 1024;
+}
+
 void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
-             cudaStream_t s) {
+             cudaStream_t s, bool split) {
   const int n = map.total();
   if (!tc_supported(n, n) || map.k1 != 0)
     throw CudaError{cudaErrorInvalidValue, "gram_tc: one block of at most 128 columns"};
@@ -387,8 +569,10 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
   if (dev < 32 && !(attr.load() & (1u << dev))) {
-    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kGramSmem));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  GramRing<false>::Smem));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  GramRing<true>::Smem));
     attr.fetch_or(1u << dev);
   }
   int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kGK - 1) / kGK, kGramChunks));
@@ -396,8 +580,12 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
   rpc = ((rpc + kGK - 1) / kGK) * kGK;
   nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
   if (rows > 0) {
-    k_tc_gram<<<nchunks, kTcThreads, kGramSmem, s>>>(X, ldx, n, rows, rpc, ws.gram_partial,
-                                                     ws.flags);
+    if (split)
+      k_tc_gram<true><<<nchunks, kTcThreads, GramRing<true>::Smem, s>>>(
+          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+    else
+      k_tc_gram<false><<<nchunks, kTcThreads, GramRing<false>::Smem, s>>>(
+          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
     SFD_LAUNCH_CHECK();
   } else {
     nchunks = 0;
@@ -406,9 +594,35 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
 }
 
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
-                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh) {
+                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh, bool split) {
   if (rows <= 0 || kout <= 0) return;
   const int n = map.total();
+  if (split) {
+    if (!tc_split_supported(n, kout) || map.k1 != 0 || Yh)
+      throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: split form needs n, kout <= 112"};
+    static std::atomic<unsigned> attr3{0};
+    int dv = 0;
+    SFD_CUDA(cudaGetDevice(&dv));
+    if (dv < 32 && !(attr3.load() & (1u << dv))) {
+      SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    220 * 1024));
+      SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    220 * 1024));
+      attr3.fetch_or(1u << dv);
+    }
+    const int Kp = (n + 7) & ~7, Np = (kout + 15) & ~15;
+    const int64_t ntiles = (rows + 127) / 128;
+    const int grid = (int)std::min<int64_t>(ntiles, 152);
+    const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
+    if (vec)
+      k_tc_gemm3<true><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
+                                                                     Np, Y, ldy, ws.flags);
+    else
+      k_tc_gemm3<false><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
+                                                                      Np, Y, ldy, ws.flags);
+    SFD_LAUNCH_CHECK();
+    return;
+  }
   if (!tc_supported(n, kout) || map.k1 != 0)
     throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: one block, n and kout at most 128"};
   if (Yh && ((ldy & 7) != 0 || ((uintptr_t)Yh & 15) != 0 || ldy < kout))

@@ -230,9 +230,10 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
 
 int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int32_t precision) {
   if (rows < 0 || k < 1 || k > kMaxEll || ldx < k || !G || (rows > 0 && !X)) return SFD_EINVAL;
-  if (precision != 0 && !(precision == 1 && tc_supported(k, k))) return SFD_EINVAL;
+  if (precision != 0 && !((precision == 1 || precision == 2) && tc_supported(k, k)))
+    return SFD_EINVAL;
   return run_dense([&](Workspace& ws, cudaStream_t s) {
-    if (precision == 1) gram_tc(X, ldx, single_map(k), rows, G, ws, s);
+    if (precision) gram_tc(X, ldx, single_map(k), rows, G, ws, s, precision == 2);
     else gram(X, ldx, single_map(k), rows, G, ws, s);
   });
 }
@@ -242,9 +243,12 @@ int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const floa
   if (rows < 0 || n < 1 || n > kMaxEll || kout < 1 || kout > kMaxEll || ldx < n || ldy < kout ||
       !T || (rows > 0 && (!X || !Y)))
     return SFD_EINVAL;
-  if (precision != 0 && !(precision == 1 && tc_supported(n, kout))) return SFD_EINVAL;
+  if (precision != 0 && !(precision == 1 && tc_supported(n, kout)) &&
+      !(precision == 2 && tc_split_supported(n, kout)))
+    return SFD_EINVAL;
   return run_dense([&](Workspace& ws, cudaStream_t s) {
-    if (precision == 1) gemm_ts_tc(X, ldx, single_map(n), rows, T, kout, Y, ldy, ws, s);
+    if (precision) gemm_ts_tc(X, ldx, single_map(n), rows, T, kout, Y, ldy, ws, s, nullptr,
+                              precision == 2);
     else gemm_ts(X, ldx, single_map(n), rows, T, kout, Y, ldy, s);
   });
 }

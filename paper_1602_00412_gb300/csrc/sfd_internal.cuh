@@ -170,13 +170,18 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
 void gram_reduce_tiles(const float* partial, int nchunks, int n, float* G, cudaStream_t s);
 // Tensor-core (tcgen05 kind::tf32, FP32 accumulate) forms of gram and
 // gemm_ts for n, kout <= 128. A wait that expires sets flags[2].
+// split: the fp32-accurate form (each value split into TF32 hi and lo parts,
+// hi*hi + hi*lo + lo*hi accumulated; ~21 significant bits); the split X * T
+// needs tc_split_supported (its operands' hi and lo parts fill shared memory).
 bool tc_supported(int n, int kout);
+bool tc_split_supported(int n, int kout);
 void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
-             cudaStream_t s);
+             cudaStream_t s, bool split = false);
 // Yh (optional): write Y as fp16 into Yh (ld ldy, a multiple of 8, >= kout;
 // columns kout..ldy-1 get 0) instead of fp32 into Y; for |entries| <= 1.
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
-                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh = nullptr);
+                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh = nullptr,
+                bool split = false);
 // Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
 // row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
 // clamped.
