@@ -77,7 +77,7 @@ typedef struct sfd_options {
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the context creates its own */
   int32_t profile;      /* 1: time every sparse-product launch with CUDA events (sfd_stats.spmm_*) */
   int32_t slots;        /* buffers in flight: each slot runs one buffer's BoostedSparseShrink on its
-                           own stream while DenseShrink folds finished buffers in order; 0: 3 */
+                           own stream while DenseShrink folds finished buffers in order; 0: 6 */
   float q_margin;       /* q_mode 1: added to the network's output before rounding up (default 1) */
   float q_tau;          /* q_mode 2: a buffer's label is the smallest q of the ladder
                            {1,2,3,4,6,8,11,16,23,32,45,64} below q_fixed whose attempt passes
@@ -200,6 +200,17 @@ int sfd_dense_shrink(int64_t rows, int64_t d, int32_t ell, const float* M, float
 int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* colidx,
                  const float* vals, int32_t k, const float* X, int32_t ldx, float* Y, int32_t ldy,
                  int32_t transpose);
+
+/* The same product with the kernel form chosen (for testing the autotuned
+ * forms, which give bit-identical results): X is fp32 (x_fp16 = 0; k <= 256,
+ * ldx, ldy multiples of 4) or fp16 (x_fp16 = 1, X holds IEEE binary16 values;
+ * k <= 128, ldx, ldy multiples of 8; products and sums in fp32); variant in
+ * [0, sfd_spmm_variant_count(x_fp16)): the forms differ in how many gathered
+ * rows each lane keeps in flight. Errors: SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA. */
+int sfd_spmm_variant_count(int32_t x_fp16);
+int sfd_csr_spmm_ex(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* colidx,
+                    const float* vals, int32_t k, const void* X, int32_t x_fp16, int32_t ldx,
+                    float* Y, int32_t ldy, int32_t transpose, int32_t variant);
 
 /* Orthonormalise the columns of X (rows x k, leading dimension ld, device) in
  * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */

@@ -21,7 +21,7 @@
 
 namespace sfd {
 
-constexpr int kDefaultSlots = 3;
+constexpr int kDefaultSlots = 6;
 constexpr int kMaxSlots = 8;
 // power counts tried when labelling a buffer for the learned form
 constexpr int kLadder[] = {1, 2, 3, 4, 6, 8, 11, 16, 23, 32, 45, 64};
@@ -370,6 +370,7 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
         C.slots.back()->profile = C.opt.profile != 0;
         C.slots.back()->mixed = C.opt.precision == 1;
         C.slots.back()->autotune = C.opt.autotune != 0;
+        C.slots.back()->choice = C.slots.front()->spmm_choice;
       } catch (const CudaError& e) {
         // fewer slots when memory is short; at least one is required
         if (e.err != cudaErrorMemoryAllocation || C.slots.empty()) throw;

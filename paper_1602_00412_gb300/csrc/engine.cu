@@ -217,7 +217,7 @@ int Slot::tune_spmm(const Csr& c, const float* X, const __half* Xh, float* Yo) {
 }
 
 void Slot::spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in, const __half* Xh) {
-  int& choice = spmm_choice[&c == &csc ? 1 : 0][Xh ? 1 : 0];
+  int& choice = this->choice[&c == &csc ? 1 : 0][Xh ? 1 : 0];
   if (choice < 0) choice = autotune ? tune_spmm(c, X, Xh, Yo) : 0;
   const int variant = choice;
   auto run = [&] {

@@ -86,6 +86,9 @@ struct Slot {
   // ([A' X (CSR), A'^T Y (CSC)] x [fp32, fp16 X]), timed on its first use
   bool autotune = false;
   int spmm_choice[2][2] = {{-1, -1}, {-1, -1}};
+  // the choices in use: this slot's own, or those of the context's first slot
+  // (slots of one context share their shapes, so one slot tunes for all)
+  int (*choice)[2] = spmm_choice;
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   VsGraphs vs_graphs;  // VerifySpectral steps, captured on first use
   // profiling of the sparse products

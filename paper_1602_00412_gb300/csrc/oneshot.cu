@@ -200,6 +200,35 @@ int sfd_csr_spmm(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* col
   }
 }
 
+int sfd_spmm_variant_count(int32_t x_fp16) { return spmm_variants(x_fp16 != 0); }
+
+int sfd_csr_spmm_ex(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* colidx,
+                    const float* vals, int32_t k, const void* X, int32_t x_fp16, int32_t ldx,
+                    float* Y, int32_t ldy, int32_t transpose_flag, int32_t variant) {
+  if (m < 1 || d < 1 || k < 1 || ldx < k || ldy < k || !rowptr || !X || !Y ||
+      variant < 0 || variant >= spmm_variants(x_fp16 != 0))
+    return SFD_EINVAL;
+  if (x_fp16 ? (k > 128 || (ldx & 7) || (ldy & 7)) : (k > kMaxEll || (ldx & 3) || (ldy & 3)))
+    return SFD_EINVAL;
+  try {
+    const int64_t nnz = checked_rowptr(rowptr, m, INT32_MAX);
+    if (nnz < 0 || (nnz > 0 && (!colidx || !vals))) return SFD_EINVAL;
+    Slot S(d, 1, m, nnz, nullptr);
+    if (!load_slot(S, m, nnz, rowptr, colidx, vals)) return SFD_EINVAL;
+    const int64_t slots = 2 * (nnz / kSplit) + 4;
+    float* partial = S.arena.alloc<float>((size_t)slots * std::max(ldx, ldy));
+    const Csr& c = transpose_flag ? S.csc : S.csr;
+    if (x_fp16)
+      spmm_h(c, static_cast<const __half*>(X), ldx, k, Y, ldy, partial, S.stream, variant);
+    else
+      spmm(c, static_cast<const float*>(X), ldx, k, Y, ldy, partial, S.stream, variant);
+    SFD_CUDA(cudaStreamSynchronize(S.stream));
+    return SFD_OK;
+  } catch (const CudaError& e) {
+    return code_of(e);
+  }
+}
+
 int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
   if (rows < 1 || k < 1 || k > kMaxEll || ld < k || !X) return SFD_EINVAL;
   DevArena A;

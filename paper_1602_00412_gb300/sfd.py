@@ -52,7 +52,8 @@ class sfd_shrink_info(ctypes.Structure):
 
 EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "sfd_merge",
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
-           "sfd_dense_shrink", "sfd_csr_spmm", "sfd_orthonormalize", "sfd_symeig",
+           "sfd_dense_shrink", "sfd_csr_spmm", "sfd_spmm_variant_count", "sfd_csr_spmm_ex",
+           "sfd_orthonormalize", "sfd_symeig",
            "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_q_model", "sfd_q_log",
            "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train", "sfd_batch_create",
            "sfd_batch_append", "sfd_batch_wait", "sfd_batch_sketch", "sfd_batch_merge_tree",
@@ -91,6 +92,8 @@ def load(path=None):
                                   vp, ctypes.POINTER(sfd_shrink_info)]
     L.sfd_dense_shrink.argtypes = [i64, i64, i32, vp, vp]
     L.sfd_csr_spmm.argtypes = [i64, i64, vp, vp, vp, i32, vp, i32, vp, i32, i32]
+    L.sfd_spmm_variant_count.argtypes = [i32]
+    L.sfd_csr_spmm_ex.argtypes = [i64, i64, vp, vp, vp, i32, vp, i32, i32, vp, i32, i32, i32]
     L.sfd_orthonormalize.argtypes = [i64, i32, vp, i32]
     L.sfd_symeig.argtypes = [i32, vp, i32, vp, vp]
     L.sfd_symeig_noalloc.argtypes = [i32, vp, i32, vp, vp]
@@ -229,6 +232,21 @@ def sfd_csr_spmm(m, d, rowptr, colidx, vals, k, X, ldx, Y, ldy, transpose):
                                ctypes.c_void_p(colidx.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
                                k, ctypes.c_void_p(X.data_ptr()), ldx, ctypes.c_void_p(Y.data_ptr()),
                                ldy, int(transpose)))
+
+
+def sfd_spmm_variant_count(x_fp16):
+    return int(load().sfd_spmm_variant_count(int(bool(x_fp16))))
+
+
+def sfd_csr_spmm_ex(m, d, rowptr, colidx, vals, k, X, ldx, Y, ldy, transpose, variant):
+    """sfd_csr_spmm with the kernel form chosen; X fp16 (torch.float16) or fp32."""
+    import torch
+    half = X.dtype == torch.float16
+    _check(load().sfd_csr_spmm_ex(m, d, ctypes.c_void_p(rowptr.data_ptr()),
+                                  ctypes.c_void_p(colidx.data_ptr()),
+                                  ctypes.c_void_p(vals.data_ptr()), k,
+                                  ctypes.c_void_p(X.data_ptr()), int(half), ldx,
+                                  ctypes.c_void_p(Y.data_ptr()), ldy, int(transpose), int(variant)))
 
 
 def sfd_orthonormalize(rows, k, X, ld):

@@ -69,6 +69,42 @@ def test_spmm_matches_fp64(lib, kind, k, transpose):
     assert np.all(err <= 1e-5 * scale + 1e-30), err.max()
 
 
+@pytest.mark.parametrize("kind", ["zipf", "edges", "tiny", "wide"])
+@pytest.mark.parametrize("k", [1, 8, 20, 50, 100, 128])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_spmm_forms_are_bit_identical(lib, kind, k, transpose):
+    # every kernel form the autotuner may pick (gathers with different
+    # unrolling) gives the same bits, and the fp16 forms match FP64 on the
+    # fp16 inputs
+    if kind == "wide":   # C2's row shape: Poisson(50) entries per row, Zipf(1.1) columns
+        X = synth.planted(20000, 5000, 50, 1.1, 5, 10.0, 0.8, 0.1, 3)
+        A, d = X.to_scipy().astype(np.float32), 5000
+    else:
+        A, d = csr_case(kind)
+    m = A.shape[0]
+    ld = (k + 7) // 8 * 8
+    rows_in = m if transpose else d
+    rng = np.random.default_rng(k + transpose)
+    X32 = np.zeros((rows_in, ld), np.float32)
+    X32[:, :k] = rng.uniform(-1, 1, (rows_in, k))
+    X16 = X32.astype(np.float16)
+    args = (m, d, dev(A.indptr, np.int32), dev(A.indices, np.int32), dev(A.data, np.float32), k)
+    n_out = d if transpose else m
+    for Xin, half in ((dev(X32), False), (dev(X16), True)):
+        outs = []
+        for v in range(lib.sfd_spmm_variant_count(half)):
+            Y = torch.full((n_out, ld), 7.0, device="cuda")
+            lib.sfd_csr_spmm_ex(*args, Xin, ld, Y, ld, transpose, v)
+            outs.append(Y.cpu().numpy())
+        for v, o in enumerate(outs[1:], 1):
+            assert np.array_equal(o[:, :k], outs[0][:, :k]), (half, v)
+        if half:
+            Af = (A.T if transpose else A).astype(np.float64)
+            want = Af @ X16[:, :k].astype(np.float64)
+            scale = abs(Af) @ np.abs(X16[:, :k].astype(np.float64))
+            assert np.all(np.abs(outs[0][:, :k] - want) <= 1e-5 * scale + 1e-30)
+
+
 def test_spmm_is_deterministic(lib):
     A, d = csr_case("edges")
     m = A.shape[0]
