@@ -200,7 +200,7 @@ int harvest_front(Ctx& C) {
   C.st.last_fro2 = v.fro2a;
   Merger& M = *C.merger;
   SFD_CUDA(cudaStreamWaitEvent(M.stream, S.done, 0));
-  M.dense_shrink(S.Bpt, S.ld, C.ell);
+  M.dense_shrink(S.Bpt, S.ld, C.ell, true);
   SFD_CUDA(cudaEventRecord(S.freed, M.stream));
   S.freed_pending = true;
   C.st.buffers++;
@@ -364,6 +364,7 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
     C.chk_fro2 = C.stage_arena.alloc<double>(1032);
     C.chk_flags = C.stage_arena.alloc<int>(4);
     C.merger.reset(new Merger(d, ell));
+    C.merger->mixed = C.opt.precision == 1;
     for (int i = 0; i < want; ++i) {
       try {
         C.slots.emplace_back(new Slot(d, ell, d, cap_nnz, nullptr));
@@ -548,7 +549,7 @@ int sfd_merge(sfd_ctx* dst, sfd_ctx* src) {
     Merger& MD = *D.merger;
     SFD_CUDA(cudaEventRecord(S.user_ev, S.merger->stream));
     SFD_CUDA(cudaStreamWaitEvent(MD.stream, S.user_ev, 0));
-    MD.dense_shrink(S.merger->B(), S.merger->ld, D.ell);  // Sec. 3.1: DSh([B_dst; B_src])
+    MD.dense_shrink(S.merger->B(), S.merger->ld, D.ell, true);  // Sec. 3.1: DSh([B_dst; B_src])
     SFD_CUDA(cudaStreamSynchronize(MD.stream));
     release_user_stream(D);
     return rc1 != SFD_OK ? rc1 : rc2;

@@ -358,11 +358,17 @@ void Merger::zero() {
   cur = 0;
 }
 
-void Merger::dense_shrink(const float* Xt, int ldx, int k1) {
+void Merger::dense_shrink(const float* Xt, int ldx, int k1, bool orthogonal_rows) {
   // Alg. 5 on the stack [B; X]: K = M M^T, top-l eigenpairs, B^T <- M^T U_l diag(s)
   const ColMap map{ell, k1, Xt, ldx};
   const int n = ell + k1;
-  gram(Bt[cur], ld, map, d, ws.small_a, ws, stream);
+  // B B^T and X X^T are diagonal when both have orthogonal rows (B = diag(s) V^T
+  // after Alg. 5, B' = diag(s) H^T P after Alg. 3): only B X^T and the row
+  // norms are formed then
+  if (mixed && orthogonal_rows && k1 >= 1 && ell <= 128 && k1 <= 128)
+    cross_gram_tc(Bt[cur], ld, ell, Xt, ldx, k1, d, ws.small_a, ws, stream);
+  else
+    gram(Bt[cur], ld, map, d, ws.small_a, ws, stream);
   symeig(ws.small_a, n, ell, ws.evals, ws.small_b, ws.eig_work, stream, true);
   shrink_weights(ws.evals, ws.small_b, n, ell, ell, 0, ws.small_a, ws.scalars, stream);
   gemm_ts(Bt[cur], ld, map, d, ws.small_a, ell, Bt[1 - cur], ld, stream);

@@ -144,10 +144,16 @@ struct Merger {
   Merger(const Merger&) = delete;
   Merger& operator=(const Merger&) = delete;
 
+  // precision 1: when both blocks have orthogonal rows, the Gram of the stack
+  // is formed on tensor cores from its cross block (split TF32, cross_gram_tc)
+  bool mixed = false;
+
   float* B() { return Bt[cur]; }
   void zero();
   // B <- DenseShrink([B; X]) with X^T given as d x k1 (leading dimension ldx).
-  void dense_shrink(const float* Xt, int ldx, int k1);
+  // orthogonal_rows: X has orthogonal rows (a sketch, or the B' of
+  // SparseShrink), as B always has (it is a DenseShrink output, or 0).
+  void dense_shrink(const float* Xt, int ldx, int k1, bool orthogonal_rows = false);
 
  private:
   void cleanup();

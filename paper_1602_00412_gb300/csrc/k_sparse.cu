@@ -456,10 +456,13 @@ __global__ void __launch_bounds__(256)
     k_spmv(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
            const int2* __restrict__ items, const int* __restrict__ item_slot,
            const int* __restrict__ n_items_ptr, const float* __restrict__ x, float* __restrict__ y,
-           float* __restrict__ partial) {
+           float* __restrict__ partial, const double* __restrict__ xscale) {
   // eight lanes per work item (four items per warp): rows and columns of a
   // buffer hold tens of entries, so a whole warp per item would idle
   const int n_items = *n_items_ptr;
+  // x is used as x * xs (xs = (float)xscale[1], exactly the product a
+  // separate scaling pass would store; 1 when xscale is null)
+  const float xs = xscale ? (float)xscale[1] : 1.f;
   const int warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3;
   if (warp_first >= n_items) return;  // whole warp past the end
   const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(256)
     const int2 it = items[item];
     seg = it.x;
     const int end = min(it.y + kSplit, ptr[seg + 1]);
-    for (int p = it.y + gl; p < end; p += 8) a = fmaf(val[p], __ldg(&x[idx[p]]), a);
+    for (int p = it.y + gl; p < end; p += 8) a = fmaf(val[p], __ldg(&x[idx[p]]) * xs, a);
   }
   a += __shfl_xor_sync(0xffffffffu, a, 4);
   a += __shfl_xor_sync(0xffffffffu, a, 2);
@@ -655,10 +658,11 @@ void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, fl
   SFD_LAUNCH_CHECK();
 }
 
-void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s) {
+void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s,
+          const double* xscale) {
   const SegWork& w = c.work;
   k_spmv<<<(w.cap_items + 31) / 32, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
-                                                 w.d_n_items, x, y, partial);
+                                                 w.d_n_items, x, y, partial, xscale);
   SFD_LAUNCH_CHECK();
   const int g2 = std::max(1, std::min((w.cap_split + 7) / 8, 2 * 152));
   k_spmv_fixup<<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split, partial,

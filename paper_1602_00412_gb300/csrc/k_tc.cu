@@ -275,6 +275,205 @@ __global__ void __launch_bounds__(kTcThreads)
   if (warp == 0) tmem_free(tmem, 128);
 }
 
+// ----------------------------------------------------------- cross Gram
+// For two blocks X1 (rows x n1) and X2 (rows x n2) whose columns are known to
+// be mutually orthogonal within each block (the rows of a sketch B, and of
+// the B' of SparseShrink, are orthogonal by construction, Alg. 3 and Alg. 5),
+// the Gram of [X1 X2] has diagonal diagonal blocks. This kernel forms the
+// cross block X1^T X2 in the split TF32 form and the squared column norms
+// of both blocks (the diagonals), per chunk of rows: partial[chunk] holds
+// the 128 x 128 cross block, then 128 norms of X1, then 128 norms of X2.
+// Rows are staged kXK = 16 at a time; a stage holds hi and lo of both tiles.
+constexpr int kXK = 16;
+constexpr int kXTile = 128 * kXK;  // floats per tile
+constexpr int kXSt = 6;            // stages in the ring
+constexpr int kXLook = kXSt - 2;
+constexpr int kXSmem = kXSt * 4 * kXTile * (int)sizeof(float);  // 192 KB
+constexpr int kXPartial = 128 * 128 + 256;                      // floats per chunk
+
+__global__ void __launch_bounds__(kTcThreads)
+    k_tc_cross(const float* __restrict__ X1, int ld1, int n1, const float* __restrict__ X2,
+               int ld2, int n2, int64_t rows, int64_t rows_per_chunk, float* __restrict__ partial,
+               int* __restrict__ flags) {
+  extern __shared__ __align__(1024) float smem[];
+  __shared__ __align__(8) uint64_t mbar[kXSt];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    for (int b = 0; b < kXSt; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[b])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, 128);
+  const int64_t r_beg = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  const int nst = r_end > r_beg ? (int)((r_end - r_beg + kXK - 1) / kXK) : 0;
+  const uint32_t sbase = smem_u32(smem);
+  // stage b: tiles hi1, lo1, hi2, lo2 at b * 4 * kXTile + {0, 1, 2, 3} * kXTile
+  const int m = tid;  // thread m copies (and splits) column m of both tiles
+  auto issue = [&](int st) {
+    const int64_t r0 = r_beg + (int64_t)st * kXK;
+    const uint32_t dst = sbase + (uint32_t)((st % kXSt) * 4 * kXTile) * 4u;
+#pragma unroll
+    for (int k = 0; k < kXK; ++k) {
+      const int64_t g = r0 + k;
+      const bool in = g < r_end;
+      const bool ok1 = in && m < n1, ok2 = in && m < n2;
+      const uint32_t o = (uint32_t)core_off(m, k, kXK) * 4u;
+      cp_async4(dst + o, ok1 ? (const void*)(X1 + g * ld1 + m) : X1, ok1 ? 4u : 0u);
+      cp_async4(dst + (uint32_t)(2 * kXTile) * 4u + o, ok2 ? (const void*)(X2 + g * ld2 + m) : X2,
+                ok2 ? 4u : 0u);
+    }
+  };
+  float sq1 = 0.f, sq2 = 0.f;  // this thread's column norms, rows in order
+  uint32_t phase_bits = 0, used_bits = 0;
+  bool ok = true;
+#pragma unroll
+  for (int st = 0; st < kXLook; ++st) {
+    if (st < nst) issue(st);
+    cp_async_commit();
+  }
+  for (int st = 0; st < nst; ++st) {
+    const int ns = st + kXLook;
+    if (ns < nst) {
+      const int b = ns % kXSt;
+      if (used_bits & (1u << b)) {  // the MMAs that read this buffer must be done
+        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+        if (!__syncthreads_and(w)) { ok = false; break; }
+        phase_bits ^= 1u << b;
+        used_bits &= ~(1u << b);
+      }
+      issue(ns);
+    }
+    cp_async_commit();
+    cp_async_wait<kXLook>();  // this thread's copies of stage st have landed
+    const int b = st % kXSt;
+    float* t = smem + b * 4 * kXTile;
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {  // X1 then X2: hi in place, lo next to it
+      float* hi = t + blk * 2 * kXTile;
+      float* lo = hi + kXTile;
+      float sq = 0.f;
+#pragma unroll
+      for (int k = 0; k < kXK; k += 4) {
+        const int o = core_off(m, k, kXK);
+        const float4 x = *reinterpret_cast<const float4*>(hi + o);
+        sq = fmaf(x.x, x.x, sq);
+        sq = fmaf(x.y, x.y, sq);
+        sq = fmaf(x.z, x.z, sq);
+        sq = fmaf(x.w, x.w, sq);
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(hi + o) = h;
+        *reinterpret_cast<float4*>(lo + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      if (blk == 0) sq1 += sq;
+      else sq2 += sq;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::);
+      const uint32_t base = sbase + (uint32_t)(b * 4 * kXTile) * 4u;
+#pragma unroll
+      for (int kk = 0; kk < kXK / 8; ++kk) {
+        const uint64_t d1h = smem_desc(base + kk * 256, 128, kXK * 32);
+        const uint64_t d1l = smem_desc(base + (uint32_t)kXTile * 4u + kk * 256, 128, kXK * 32);
+        const uint64_t d2h = smem_desc(base + (uint32_t)(2 * kXTile) * 4u + kk * 256, 128, kXK * 32);
+        const uint64_t d2l = smem_desc(base + (uint32_t)(3 * kXTile) * 4u + kk * 256, 128, kXK * 32);
+        mma_tf32(tmem, d1h, d2h, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, d1h, d2l, idesc, 1u);
+        mma_tf32(tmem, d1l, d2h, idesc, 1u);
+      }
+      mma_commit(&mbar[b]);
+    }
+    used_bits |= 1u << b;
+  }
+  cp_async_wait<0>();
+  if (ok) {
+    bool all = true;
+    for (int b = 0; b < kXSt; ++b)
+      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u) && all;
+    ok = __syncthreads_and(all);
+    if (ok) used_bits = 0;
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&flags[2], 1);
+    for (int b = 0; b < kXSt; ++b)  // bounded: let MMAs in flight finish before freeing
+      if (used_bits & (1u << b)) mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  __syncthreads();
+  float* out = partial + (int64_t)blockIdx.x * kXPartial;
+  const int row = warp * 32 + lane;
+  const bool have = ok && nst > 0;
+  for (int c0 = 0; c0 < n2; c0 += 16) {
+    float v[16];
+    if (have) {
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    }
+    if (row < n1) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(&out[row * 128 + c0 + j]) =
+            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+  }
+  out[128 * 128 + m] = have ? sq1 : 0.f;
+  out[128 * 128 + 128 + m] = have ? sq2 : 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 128);
+}
+
+// G ((n1 + n2) x (n1 + n2), row-major) from the chunk partials of k_tc_cross:
+// one thread per entry of the first n1 rows (mirrored into the first n1
+// columns) and per entry of the last n2 x n2 block; chunks summed in order.
+__global__ void k_cross_reduce(const float* __restrict__ partial, int nchunks, int n1, int n2,
+                               float* __restrict__ G) {
+  const int N = n1 + n2;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t top = (int64_t)n1 * N;
+  if (e >= top + (int64_t)n2 * n2) return;
+  int i, j, off;
+  bool zero = false;
+  if (e < top) {
+    i = (int)(e / N);
+    j = (int)(e % N);
+    if (j < n1) {
+      zero = i != j;
+      off = 128 * 128 + i;
+    } else {
+      off = i * 128 + (j - n1);
+    }
+  } else {
+    const int64_t f = e - top;
+    i = n1 + (int)(f / n2);
+    j = n1 + (int)(f % n2);
+    zero = i != j;
+    off = 128 * 128 + 128 + (i - n1);
+  }
+  float s0 = 0.f, s1 = 0.f;
+  if (!zero) {
+    int ch = 0;
+    for (; ch + 1 < nchunks; ch += 2) {
+      s0 += partial[(int64_t)ch * kXPartial + off];
+      s1 += partial[(int64_t)(ch + 1) * kXPartial + off];
+    }
+    if (ch < nchunks) s0 += partial[(int64_t)ch * kXPartial + off];
+  }
+  const float g = s0 + s1;
+  G[(int64_t)i * N + j] = g;
+  if (e < top && j >= n1) G[(int64_t)j * N + i] = g;
+}
+
 // ----------------------------------------------------------------- X * T
 // Y[rows, 0:kout] = X[rows, 0:n] T (T: n x kout, row-major). T^T (Np x Kp,
 // n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA. 128-row tiles
@@ -548,6 +747,36 @@ __global__ void __launch_bounds__(kTcThreads)
 }
 
 }  // namespace
+
+void cross_gram_tc(const float* X1, int ld1, int n1, const float* X2, int ld2, int n2,
+                   int64_t rows, float* G, Workspace& ws, cudaStream_t s) {
+  if (n1 < 1 || n1 > 128 || n2 < 0 || n2 > 128)
+    throw CudaError{cudaErrorInvalidValue, "cross_gram_tc: blocks of at most 128 columns"};
+  static std::atomic<unsigned> attr{0};
+  int dev = 0;
+  SFD_CUDA(cudaGetDevice(&dev));
+  if (dev < 32 && !(attr.load() & (1u << dev))) {
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_cross, cudaFuncAttributeMaxDynamicSharedMemorySize, kXSmem));
+    attr.fetch_or(1u << dev);
+  }
+  int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kXK - 1) / kXK, kGramChunks));
+  int64_t rpc = (rows + nchunks - 1) / nchunks;
+  rpc = ((rpc + kXK - 1) / kXK) * kXK;
+  nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
+  if ((int64_t)nchunks * kXPartial > (int64_t)320 * 128 * 128)
+    throw CudaError{cudaErrorInvalidValue, "cross_gram_tc: partial buffer"};
+  if (rows > 0) {
+    k_tc_cross<<<nchunks, kTcThreads, kXSmem, s>>>(X1, ld1, n1, X2 ? X2 : X1, ld2, n2, rows, rpc,
+                                                   ws.gram_partial, ws.flags);
+    SFD_LAUNCH_CHECK();
+  } else {
+    nchunks = 0;
+  }
+  const int N = n1 + n2;
+  const int64_t ne = (int64_t)n1 * N + (int64_t)n2 * n2;
+  k_cross_reduce<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(ws.gram_partial, nchunks, n1, n2, G);
+  SFD_LAUNCH_CHECK();
+}
 
 bool tc_supported(int n, int kout) { return n >= 1 && n <= 128 && kout >= 1 && kout <= 128; }
 

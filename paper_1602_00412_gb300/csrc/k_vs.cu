@@ -5,8 +5,8 @@
 // sum is <= 0 (the host compares).
 //
 // One step: u = A' x (CSR), w = B' x (reduction over the d rows of B'^T),
-// v = A'^T u (CSC) - B'^T w, ||v||, x <- v / ||v||. Every reduction runs in a
-// fixed order (deterministic).
+// v = A'^T u (CSC) - B'^T w, ||v||, x <- v / ||v|| (the division is applied
+// where x is read). Every reduction runs in a fixed order (deterministic).
 #include <math.h>
 
 #include <algorithm>
@@ -44,12 +44,11 @@ __global__ void k_norm2_partial(const float* __restrict__ x, int64_t n, float* _
 
 // scal[0] logsum, scal[1] inverse norm of the current x, scal[2] 1 if some C x_t was 0.
 // mode 0: initial normalisation (no log term); mode 1: a power step with factor *scale.
-__global__ void k_norm_finalize(const float* __restrict__ part, int nb,
-                                const double* __restrict__ scale_ptr, int mode,
-                                double* __restrict__ scal) {
-  __shared__ double sh[256];
+// Run by one block of 256 threads (sh: 256 doubles of shared memory).
+__device__ void norm_finalize_block(const float* part, int nb, const double* scale_ptr, int mode,
+                                    double* scal, double* sh) {
   double a = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) a += (double)part[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) a += (double)__ldcg(&part[i]);
   sh[threadIdx.x] = a;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -69,11 +68,11 @@ __global__ void k_norm_finalize(const float* __restrict__ part, int nb,
   }
 }
 
-__global__ void k_scale(float* __restrict__ x, int64_t n, const double* __restrict__ scal) {
-  const float s = (float)scal[1];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] *= s;
+__global__ void __launch_bounds__(256)
+    k_norm_finalize(const float* __restrict__ part, int nb, const double* __restrict__ scale_ptr,
+                    int mode, double* __restrict__ scal) {
+  __shared__ double sh[256];
+  norm_finalize_block(part, nb, scale_ptr, mode, scal, sh);
 }
 
 // wpart[b][c] = sum over the rows j of stripe b of Bt[j][c] * x[j]. A warp
@@ -82,8 +81,10 @@ __global__ void k_scale(float* __restrict__ x, int64_t n, const double* __restri
 // partial sums are added in warp order (fixed).
 __global__ void __launch_bounds__(256)
     k_btx_partial(const float* __restrict__ Bt, int ld, int ell, int64_t d,
-                  const float* __restrict__ x, float* __restrict__ wpart) {
+                  const float* __restrict__ x, const double* __restrict__ xscale,
+                  float* __restrict__ wpart) {
   __shared__ float4 red[8][kMaxEll / 4];
+  const float xs = (float)xscale[1];  // x is read as x * xs (its pending normalisation)
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int nvec = (ell + 3) >> 2;
   const int64_t rows = (d + gridDim.x - 1) / gridDim.x;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256)
       for (; j + 24 < j1; j += 32) {  // four rows of this warp in flight
         const float4 b0 = B4[(j + 0) * ld4 + c4], b1 = B4[(j + 8) * ld4 + c4];
         const float4 b2 = B4[(j + 16) * ld4 + c4], b3 = B4[(j + 24) * ld4 + c4];
-        const float x0 = x[j], x1 = x[j + 8], x2 = x[j + 16], x3 = x[j + 24];
+        const float x0 = x[j] * xs, x1 = x[j + 8] * xs, x2 = x[j + 16] * xs, x3 = x[j + 24] * xs;
         a.x = fmaf(b0.x, x0, a.x); a.y = fmaf(b0.y, x0, a.y); a.z = fmaf(b0.z, x0, a.z); a.w = fmaf(b0.w, x0, a.w);
         a.x = fmaf(b1.x, x1, a.x); a.y = fmaf(b1.y, x1, a.y); a.z = fmaf(b1.z, x1, a.z); a.w = fmaf(b1.w, x1, a.w);
         a.x = fmaf(b2.x, x2, a.x); a.y = fmaf(b2.y, x2, a.y); a.z = fmaf(b2.z, x2, a.z); a.w = fmaf(b2.w, x2, a.w);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256)
       }
       for (; j < j1; j += 8) {
         const float4 b0 = B4[j * ld4 + c4];
-        const float x0 = x[j];
+        const float x0 = x[j] * xs;
         a.x = fmaf(b0.x, x0, a.x); a.y = fmaf(b0.y, x0, a.y); a.z = fmaf(b0.z, x0, a.z); a.w = fmaf(b0.w, x0, a.w);
       }
     }
@@ -139,12 +140,19 @@ __global__ void __launch_bounds__(256)
 // v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block
 // (fixed grid). A warp takes four rows at a time: their float4 row pieces and
 // the four v entries are loaded before any arithmetic, so the loads overlap;
-// lane 0 keeps the block's squares in row order.
+// lane 0 keeps the block's squares in row order. The last block to finish
+// (a ticket on *counter, reset after use) adds the parts up and updates the
+// log-sum and the inverse norm of v (norm_finalize_block, mode 1), so the
+// step needs no separate reduction launch.
 __global__ void __launch_bounds__(256)
     k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
-               const float* __restrict__ w, float* __restrict__ part) {
+               const float* __restrict__ w, float* __restrict__ part,
+               const double* __restrict__ scale_ptr, double* __restrict__ scal,
+               unsigned* __restrict__ counter) {
   __shared__ float4 ws[kMaxEll / 4];
   __shared__ float red[8];
+  __shared__ double sh[256];
+  __shared__ bool last;
   const int nvec = (ell + 3) >> 2;  // <= 64
   for (int c = threadIdx.x; c < kMaxEll / 4; c += blockDim.x) {
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -202,6 +210,14 @@ __global__ void __launch_bounds__(256)
     float t = 0.f;
     for (int i = 0; i < 8; ++i) t += red[i];
     part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    norm_finalize_block(part, gridDim.x, scale_ptr, 1, scal, sh);
+    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
@@ -249,19 +265,19 @@ namespace {
 
 // One power step x -> v (u = A'x, w = B'x, v = A'^T u - B'^T w, log ||v||,
 // v /= ||v||); the caller swaps x and v.
+// x is held unnormalised: its consumers (A' x, B' x) read x * scal[1], the
+// value a separate scaling pass would have stored, and k_v_update's last
+// block sets scal[1] for the new v.
 void vs_step(const VsArgs& a, Workspace& ws, float* x, float* u, float* v, float* w, float* part,
-             double* scal, cudaStream_t s) {
-  spmv(*a.csr, x, u, ws.partial_rows, s);
-  k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, ws.wpart);
+             double* scal, unsigned* counter, cudaStream_t s) {
+  spmv(*a.csr, x, u, ws.partial_rows, s, scal);
+  k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, scal, ws.wpart);
   SFD_LAUNCH_CHECK();
   k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
   SFD_LAUNCH_CHECK();
   spmv(*a.csc, u, v, ws.partial_rows, s);
-  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part);
-  SFD_LAUNCH_CHECK();
-  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, a.scale_dev, 1, scal);
-  SFD_LAUNCH_CHECK();
-  k_scale<<<kVsBlocks, 256, 0, s>>>(v, a.d, scal);
+  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, a.scale_dev, scal,
+                                       counter);
   SFD_LAUNCH_CHECK();
 }
 
@@ -269,10 +285,11 @@ void vs_step(const VsArgs& a, Workspace& ws, float* x, float* u, float* v, float
 // made while capturing are taken off the launch counter again: the kernels
 // run when the graph is replayed, and each replay is counted then.
 cudaGraphExec_t capture(cudaStream_t s, int steps, const VsArgs& a, Workspace& ws, float* x,
-                        float* u, float* v, float* w, float* part, double* scal, size_t* nodes) {
+                        float* u, float* v, float* w, float* part, double* scal, unsigned* counter,
+                        size_t* nodes) {
   SFD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   for (int t = 0; t < steps; ++t) {
-    vs_step(a, ws, x, u, v, w, part, scal, s);
+    vs_step(a, ws, x, u, v, w, part, scal, counter, s);
     std::swap(x, v);
   }
   cudaGraph_t g = nullptr;
@@ -296,25 +313,25 @@ void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s, VsGraphs* g
   float* w = ws.wpart + kVsBlocks * kMaxEll;  // ell
   float* part = ws.wpart + kVsBlocks * kMaxEll + kMaxEll;  // kVsBlocks
   double* scal = ws.scalars + kSlogsum;
+  unsigned* counter = reinterpret_cast<unsigned*>(ws.flags + 8);  // k_v_update's tickets
   SFD_CUDA(cudaMemsetAsync(scal, 0, 4 * sizeof(double), s));
+  SFD_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
   launch_gauss_fill(x, a.d, 1, 1, a.seed, a.b, a.r, 2 /* tag of Alg. 6's x */, s);
   k_norm2_partial<<<kVsBlocks, 256, 0, s>>>(x, a.d, part);
   SFD_LAUNCH_CHECK();
-  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, nullptr, 0, scal);
-  SFD_LAUNCH_CHECK();
-  k_scale<<<kVsBlocks, 256, 0, s>>>(x, a.d, scal);
+  k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, nullptr, 0, scal);  // x stays unscaled
   SFD_LAUNCH_CHECK();
   if (!graphs) {
     for (int t = 0; t < a.p; ++t) {
-      vs_step(a, ws, x, u, v, w, part, scal, s);
+      vs_step(a, ws, x, u, v, w, part, scal, counter, s);
       std::swap(x, v);
     }
     return;
   }
   if (!graphs->one) {
     size_t n1 = 0, n2 = 0;
-    graphs->one = capture(s, 1, a, ws, x, u, v, w, part, scal, &n1);
-    graphs->two = capture(s, 2, a, ws, x, u, v, w, part, scal, &n2);
+    graphs->one = capture(s, 1, a, ws, x, u, v, w, part, scal, counter, &n1);
+    graphs->two = capture(s, 2, a, ws, x, u, v, w, part, scal, counter, &n2);
     graphs->kernels_per_step = (int)n1;
   }
   // x starts in vec0 and is back there after every two steps

@@ -141,7 +141,9 @@ inline int spmm_variants(bool half) { return half ? 3 : 2; }
 void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, float* partial,
             cudaStream_t s, int variant = 0);
 // y[seg] = scale_ptr? * sum val * x[idx]
-void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s);
+// xscale (nullable): x is read as x * (float)xscale[1] (a pending normalisation)
+void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s,
+          const double* xscale = nullptr);
 
 // ----------------------------------------------------------------- dense ops
 // Philox4x64-10 Gaussian fill: out[i*ld + j] = normal #(i*cols + j) of (seed,b,r,tag).
@@ -177,6 +179,12 @@ bool tc_supported(int n, int kout);
 bool tc_split_supported(int n, int kout);
 void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Workspace& ws,
              cudaStream_t s, bool split = false);
+// G = [X1 X2]^T [X1 X2] ((n1 + n2) x (n1 + n2) row-major) for blocks whose
+// columns are mutually orthogonal within each block: only the cross block
+// X1^T X2 (split TF32) and the squared column norms are formed; the other
+// entries of the diagonal blocks are 0. n1 in [1, 128], n2 in [0, 128].
+void cross_gram_tc(const float* X1, int ld1, int n1, const float* X2, int ld2, int n2,
+                   int64_t rows, float* G, Workspace& ws, cudaStream_t s);
 // Yh (optional): write Y as fp16 into Yh (ld ldy, a multiple of 8, >= kout;
 // columns kout..ldy-1 get 0) instead of fp32 into Y; for |entries| <= 1.
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
