@@ -32,6 +32,9 @@ void alloc_work(DevArena& A, SegWork& w, int64_t nseg, int64_t nnz) {
   w.cap_split = (int)std::min<int64_t>(nseg, nnz / kSplit + 1) + 1;
   w.items = A.alloc<int2>(w.cap_items);
   w.item_slot = A.alloc<int>(w.cap_items);
+  w.item_split = A.alloc<int>(w.cap_items);
+  w.split_ticket = A.alloc<unsigned>(w.cap_split);
+  SFD_CUDA(cudaMemset(w.split_ticket, 0, (size_t)w.cap_split * sizeof(unsigned)));
   w.split_seg = A.alloc<int>(std::max<int64_t>(nseg, 1) + 1);
   w.split_first = A.alloc<int>(std::max<int64_t>(nseg, 1) + 1);
   w.split_count = A.alloc<int>(std::max<int64_t>(nseg, 1) + 1);

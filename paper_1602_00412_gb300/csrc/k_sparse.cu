@@ -270,8 +270,8 @@ __global__ void k_count_items(const int* __restrict__ ptr, int nseg, int* __rest
 __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* __restrict__ item_off,
                              const int* __restrict__ slot_off, const int* __restrict__ split_off,
                              int2* __restrict__ items, int* __restrict__ item_slot,
-                             int* __restrict__ split_seg, int* __restrict__ split_first,
-                             int* __restrict__ split_count) {
+                             int* __restrict__ item_split, int* __restrict__ split_seg,
+                             int* __restrict__ split_first, int* __restrict__ split_count) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
   int b = ptr[s];
@@ -280,6 +280,7 @@ __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* _
   for (int t = 0; t < k; ++t) {
     items[o + t] = make_int2(s, b + t * kSplit);
     item_slot[o + t] = k > 1 ? slot_off[s] + t : -1;
+    item_split[o + t] = k > 1 ? split_off[s] : -1;
   }
   if (k > 1) {
     int q = split_off[s];
@@ -452,13 +453,20 @@ __global__ void __launch_bounds__(32 * kFixWarps)
 }
 
 // ------------------------------------------------------------------- SpMV
+// Eight lanes per work item (four items per warp): rows and columns of a
+// buffer hold tens of entries, so a whole warp per item would idle. An item
+// of a split segment stores its partial sum and takes a ticket on the
+// segment's counter; the item whose ticket completes the segment adds the
+// partials up (its eight lanes take every eighth partial, in order, then a
+// fixed shuffle tree), writes y and resets the counter, so no second launch
+// is needed and the sum does not depend on which item finishes last.
 __global__ void __launch_bounds__(256)
     k_spmv(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
            const int2* __restrict__ items, const int* __restrict__ item_slot,
+           const int* __restrict__ item_split, const int* __restrict__ split_first,
+           const int* __restrict__ split_count, unsigned* __restrict__ split_ticket,
            const int* __restrict__ n_items_ptr, const float* __restrict__ x, float* __restrict__ y,
            float* __restrict__ partial, const double* __restrict__ xscale) {
-  // eight lanes per work item (four items per warp): rows and columns of a
-  // buffer hold tens of entries, so a whole warp per item would idle
   const int n_items = *n_items_ptr;
   // x is used as x * xs (xs = (float)xscale[1], exactly the product a
   // separate scaling pass would store; 1 when xscale is null)
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(256)
   const int warp_first = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3;
   if (warp_first >= n_items) return;  // whole warp past the end
   const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  const int gl = threadIdx.x & 7;
+  const int gl = threadIdx.x & 7, lead = threadIdx.x & 31 & ~7;
   const bool live = item < n_items;
   float a = 0.f;
   int seg = 0;
@@ -479,29 +487,35 @@ __global__ void __launch_bounds__(256)
   a += __shfl_xor_sync(0xffffffffu, a, 4);
   a += __shfl_xor_sync(0xffffffffu, a, 2);
   a += __shfl_xor_sync(0xffffffffu, a, 1);
+  int q = -1;
+  unsigned taken = 0;
   if (live && gl == 0) {
     const int slot = item_slot[item];
-    if (slot < 0)
+    if (slot < 0) {
       y[seg] = a;
-    else
+    } else {
       partial[slot] = a;
+      __threadfence();
+      q = item_split[item];
+      taken = atomicAdd(&split_ticket[q], 1u) + 1u;
+    }
   }
-}
-
-// One warp per split segment (grid-stride): lane-strided partial sums, then a
-// fixed shuffle tree.
-__global__ void k_spmv_fixup(const int* __restrict__ split_seg, const int* __restrict__ split_first,
-                             const int* __restrict__ split_count, const int* __restrict__ n_split_ptr,
-                             const float* __restrict__ partial, float* __restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int n_split = *n_split_ptr;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_split; w += nwarps) {
-    const int f = split_first[w], c = split_count[w];
-    float a = 0.f;
-    for (int t = lane; t < c; t += 32) a += partial[f + t];
-    a = warp_sum(a);
-    if (lane == 0) y[split_seg[w]] = a;
+  q = __shfl_sync(0xffffffffu, q, lead);
+  taken = __shfl_sync(0xffffffffu, taken, lead);
+  int f = 0, c = 0;
+  if (q >= 0 && taken == (unsigned)split_count[q]) {  // this item completed the segment
+    f = split_first[q];
+    c = taken;
+    __threadfence();
+  }
+  float b = 0.f;
+  for (int t = gl; t < c; t += 8) b += __ldcg(&partial[f + t]);
+  b += __shfl_xor_sync(0xffffffffu, b, 4);
+  b += __shfl_xor_sync(0xffffffffu, b, 2);
+  b += __shfl_xor_sync(0xffffffffu, b, 1);
+  if (c > 0 && gl == 0) {
+    y[seg] = b;
+    split_ticket[q] = 0u;
   }
 }
 
@@ -586,8 +600,8 @@ void build_work(Csr& c, cudaStream_t s) {
   exclusive_scan(cnt_slots, n, slot_off, tmp, s);
   exclusive_scan(cnt_split, n, split_off, tmp, s);
   k_fill_items<<<(n + 255) / 256, 256, 0, s>>>(c.ptr, n, item_off, slot_off, split_off, w.items,
-                                               w.item_slot, w.split_seg, w.split_first,
-                                               w.split_count);
+                                               w.item_slot, w.item_split, w.split_seg,
+                                               w.split_first, w.split_count);
   SFD_LAUNCH_CHECK();
 }
 
@@ -662,11 +676,9 @@ void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s
           const double* xscale) {
   const SegWork& w = c.work;
   k_spmv<<<(w.cap_items + 31) / 32, 256, 0, s>>>(c.ptr, c.idx, c.val, w.items, w.item_slot,
-                                                 w.d_n_items, x, y, partial, xscale);
-  SFD_LAUNCH_CHECK();
-  const int g2 = std::max(1, std::min((w.cap_split + 7) / 8, 2 * 152));
-  k_spmv_fixup<<<g2, 256, 0, s>>>(w.split_seg, w.split_first, w.split_count, w.d_n_split, partial,
-                                  y);
+                                                 w.item_split, w.split_first, w.split_count,
+                                                 w.split_ticket, w.d_n_items, x, y, partial,
+                                                 xscale);
   SFD_LAUNCH_CHECK();
 }
 

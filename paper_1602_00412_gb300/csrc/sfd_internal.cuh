@@ -68,6 +68,8 @@ extern unsigned long long g_kernel_launches;
 struct SegWork {
   int2* items = nullptr;     // (segment, begin) ; end = min(begin + kSplit, ptr[seg+1])
   int* item_slot = nullptr;  // -1: item covers its whole segment, else partial slot
+  int* item_split = nullptr; // -1, else the split segment (index into split_*) of the item
+  unsigned* split_ticket = nullptr;  // per split segment: items done (0 between launches)
   int* split_seg = nullptr;  // segments cut into several items
   int* split_first = nullptr;// first item of each split segment
   int* split_count = nullptr;// items of each split segment
