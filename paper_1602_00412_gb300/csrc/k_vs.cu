@@ -6,7 +6,8 @@
 //
 // One step: u = A' x (CSR), w = B' x (reduction over the d rows of B'^T),
 // v = A'^T u (CSC) - B'^T w, ||v||, x <- v / ||v|| (the division is applied
-// where x is read). Every reduction runs in a fixed order (deterministic).
+// where x is read, and B' x is formed while v is written, so B'^T is read
+// once per step). Every reduction runs in a fixed order (deterministic).
 #include <math.h>
 
 #include <algorithm>
@@ -17,7 +18,9 @@ namespace sfd {
 
 namespace {
 
-constexpr int kVsBlocks = 512;   // fixed grids: every reduction has a fixed order
+// fixed grids, so every reduction has a fixed order; three blocks of
+// k_v_update per SM (its register budget) make one wave on 152 SMs
+constexpr int kVsBlocks = 3 * 152;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -84,7 +87,8 @@ __global__ void __launch_bounds__(256)
                   const float* __restrict__ x, const double* __restrict__ xscale,
                   float* __restrict__ wpart) {
   __shared__ float4 red[8][kMaxEll / 4];
-  const float xs = (float)xscale[1];  // x is read as x * xs (its pending normalisation)
+  // x is read as x * xs (its pending normalisation; 1 when xscale is null)
+  const float xs = xscale ? (float)xscale[1] : 1.f;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int nvec = (ell + 3) >> 2;
   const int64_t rows = (d + gridDim.x - 1) / gridDim.x;
@@ -120,9 +124,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// w[c] = sum_b wpart[b][c] : one block per column c, fixed-order tree
+// w[c] = s * sum_b wpart[b][c] (s = (float)scal[1], the pending normalisation
+// of the x the partials were formed from): one block per column c,
+// fixed-order tree
 __global__ void __launch_bounds__(256)
-    k_btx_reduce(const float* __restrict__ wpart, int nb, int ell, float* __restrict__ w) {
+    k_btx_reduce(const float* __restrict__ wpart, int nb, int ell, const double* __restrict__ scal,
+                 float* __restrict__ w) {
   const int c = blockIdx.x;
   float a = 0.f;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) a += wpart[b * ell + c];
@@ -133,23 +140,28 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) {
     float t = 0.f;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    w[c] = t;
+    w[c] = t * (float)scal[1];
   }
 }
 
 // v[j] -= sum_c Bt[j][c] w[c]; part[block] = sum of v[j]^2 of the block
 // (fixed grid). A warp takes four rows at a time: their float4 row pieces and
 // the four v entries are loaded before any arithmetic, so the loads overlap;
-// lane 0 keeps the block's squares in row order. The last block to finish
-// (a ticket on *counter, reset after use) adds the parts up and updates the
-// log-sum and the inverse norm of v (norm_finalize_block, mode 1), so the
-// step needs no separate reduction launch.
-__global__ void __launch_bounds__(256)
+// lane 0 keeps the block's squares in row order. With the rows of B'^T in
+// registers, the warps also form the next step's B' v partials
+// (wpart[block][c] = sum over the block's rows of Bt[j][c] v[j], v not yet
+// normalised: k_btx_reduce applies the norm), so B'^T is read once per
+// step. The last block to finish (a ticket on *counter, reset after use)
+// adds the parts up and updates the log-sum and the inverse norm of v
+// (norm_finalize_block, mode 1), so the step needs no separate reduction
+// launch.
+__global__ void __launch_bounds__(256, 3)
     k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
-               const float* __restrict__ w, float* __restrict__ part,
+               const float* __restrict__ w, float* __restrict__ part, float* __restrict__ wpart,
                const double* __restrict__ scale_ptr, double* __restrict__ scal,
                unsigned* __restrict__ counter) {
   __shared__ float4 ws[kMaxEll / 4];
+  __shared__ float4 red4[8][kMaxEll / 4];
   __shared__ float red[8];
   __shared__ double sh[256];
   __shared__ bool last;
@@ -171,6 +183,7 @@ __global__ void __launch_bounds__(256)
   const float4 q1 = lane + 32 < nvec ? ws[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float acc2 = 0.f;
+  float4 wa0 = z4, wa1 = z4;  // next step's B' v partials, columns lane and lane + 32
   for (int64_t j = ((int64_t)blockIdx.x * 8 + wp) * 4; j < d; j += nwarps * 4) {
     float4 b0[4], b1[4];
     float vv[4];
@@ -194,18 +207,35 @@ __global__ void __launch_bounds__(256)
       t = fmaf(b1[r].w, q1.w, t);
       s[r] = warp_sum(t);
     }
+    float nv[4];  // the new v (lane 0; 0 past d)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) nv[r] = j + r < d ? vv[r] - s[r] : 0.f;
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (j + r < d) {
-          const float nv = vv[r] - s[r];
-          v[j + r] = nv;
-          acc2 = fmaf(nv, nv, acc2);
+          v[j + r] = nv[r];
+          acc2 = fmaf(nv[r], nv[r], acc2);
         }
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float y = __shfl_sync(0xffffffffu, nv[r], 0);
+      wa0.x = fmaf(b0[r].x, y, wa0.x); wa0.y = fmaf(b0[r].y, y, wa0.y);
+      wa0.z = fmaf(b0[r].z, y, wa0.z); wa0.w = fmaf(b0[r].w, y, wa0.w);
+      wa1.x = fmaf(b1[r].x, y, wa1.x); wa1.y = fmaf(b1[r].y, y, wa1.y);
+      wa1.z = fmaf(b1[r].z, y, wa1.z); wa1.w = fmaf(b1[r].w, y, wa1.w);
+    }
   }
+  red4[wp][lane] = wa0;
+  red4[wp][lane + 32] = wa1;
   if (lane == 0) red[wp] = acc2;
   __syncthreads();
+  for (int c = threadIdx.x; c < ell; c += blockDim.x) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += reinterpret_cast<const float*>(&red4[i][0])[c];
+    wpart[blockIdx.x * ell + c] = t;
+  }
   if (threadIdx.x == 0) {
     float t = 0.f;
     for (int i = 0; i < 8; ++i) t += red[i];
@@ -268,16 +298,16 @@ namespace {
 // x is held unnormalised: its consumers (A' x, B' x) read x * scal[1], the
 // value a separate scaling pass would have stored, and k_v_update's last
 // block sets scal[1] for the new v.
+// ws.wpart holds the B' x partials of the unnormalised x on entry (from the
+// preamble or the previous step's k_v_update) and those of the new v on exit.
 void vs_step(const VsArgs& a, Workspace& ws, float* x, float* u, float* v, float* w, float* part,
              double* scal, unsigned* counter, cudaStream_t s) {
   spmv(*a.csr, x, u, ws.partial_rows, s, scal);
-  k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, scal, ws.wpart);
-  SFD_LAUNCH_CHECK();
-  k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, w);
+  k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, scal, w);
   SFD_LAUNCH_CHECK();
   spmv(*a.csc, u, v, ws.partial_rows, s);
-  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, a.scale_dev, scal,
-                                       counter);
+  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, ws.wpart, a.scale_dev,
+                                       scal, counter);
   SFD_LAUNCH_CHECK();
 }
 
@@ -320,6 +350,8 @@ void verify_spectral(const VsArgs& a, Workspace& ws, cudaStream_t s, VsGraphs* g
   k_norm2_partial<<<kVsBlocks, 256, 0, s>>>(x, a.d, part);
   SFD_LAUNCH_CHECK();
   k_norm_finalize<<<1, 256, 0, s>>>(part, kVsBlocks, nullptr, 0, scal);  // x stays unscaled
+  SFD_LAUNCH_CHECK();
+  k_btx_partial<<<kVsBlocks, 256, 0, s>>>(a.Bt, a.ld, a.ell, a.d, x, nullptr, ws.wpart);
   SFD_LAUNCH_CHECK();
   if (!graphs) {
     for (int t = 0; t < a.p; ++t) {
