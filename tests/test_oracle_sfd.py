@@ -386,6 +386,35 @@ def test_merge_identity_and_bounds():
     assert hi <= metrics.fd_bound(A, 10, 0)
 
 
+def test_shrink_outputs_have_orthogonal_rows():
+    # The reading behind the GPU's cross-block Gram in DenseShrink: B' of
+    # Alg. 3 and B of Alg. 5 have orthogonal rows, so the Gram of the stack
+    # [B; B'] is [[diag, B B'^T], [B' B^T, diag]], and DenseShrink formed from
+    # that block form equals Alg. 5 on the stack.
+    d, ell = 300, 12
+    A = synth.planted(900, d, 15, 1.1, 6, 10.0, 0.8, 0.1, 4).to_scipy().astype(np.float64)
+    G = philox.gaussian_G(0, 0, 0, d, ell)
+    Bp, _ = O.sparse_shrink(A, ell, 6, G)
+    rng = np.random.default_rng(5)
+    B = O.dense_shrink(rng.standard_normal((2 * ell, d)), ell)
+    for R in (Bp, B):
+        K = R @ R.T
+        off = K - np.diag(np.diag(K))
+        assert np.max(np.abs(off)) <= 1e-10 * np.max(np.diag(K))
+    M = np.vstack([B, Bp])
+    K = np.zeros((2 * ell, 2 * ell))
+    K[:ell, :ell] = np.diag(np.sum(B * B, axis=1))
+    K[ell:, ell:] = np.diag(np.sum(Bp * Bp, axis=1))
+    K[:ell, ell:] = B @ Bp.T
+    K[ell:, :ell] = K[:ell, ell:].T
+    w, U = np.linalg.eigh(K)
+    order = np.argsort(w)[::-1][:ell]
+    w, U = np.maximum(w[order], 0.0), U[:, order]
+    wt = np.sqrt(np.maximum(w - w[-1], 0.0)) / np.sqrt(np.where(w > 0, w, 1.0))
+    Bnew = (wt[:, None] * U.T) @ M
+    assert metrics.bbt_rel_diff(Bnew, O.dense_shrink(M, ell)) <= 1e-9
+
+
 def test_bbt_rel_diff_matches_dense():
     rng = np.random.default_rng(3)
     B1, B2 = rng.standard_normal((5, 30)), rng.standard_normal((5, 30))
