@@ -98,7 +98,9 @@ struct Workspace {
   float* evals = nullptr;         // kMaxEig
   float* eig_work = nullptr;      // eigensolver scratch
   double* scalars = nullptr;      // device scalars (norms, logs)
-  int* flags = nullptr;           // device status words
+  int* flags = nullptr;           // device status words (16): [0] bad input entry,
+                                  // [1] clamped Cholesky pivots, [2] a bounded wait
+                                  // expired, [8] VerifySpectral's block tickets
   // sparse helpers
   int* tmp_i0 = nullptr;
   int* tmp_i1 = nullptr;
