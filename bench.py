@@ -68,6 +68,24 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def over_ranks(x, world, op="max"):
+    """x reduced over the ranks of the process group ("max" or "sum"); x itself
+    when world == 1. Host-side (gloo): timings and unit counts only."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_all_ranks, steps, ms):
+    """Units per second of the whole job: every rank's units of `steps` steps
+    over the slowest rank's time (ms)."""
+    return units_all_ranks * steps / (ms / 1e3)
+
+
 def make_stream(rows, seed):
     from paper_1602_00412_gb300 import synth
     w = WORKLOAD
@@ -311,12 +329,7 @@ def ours_arm(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return over_ranks(e0.elapsed_time(e1), world, "max")
 
     for _ in range(args.warmup):
         step_device()
@@ -333,9 +346,9 @@ def ours_arm(args, rank, world, local):
             step_host()
         ms_e2e = timed(step_host, args.steps)
     B = B_d.cpu().numpy()
-    nnz_all = X.nnz * world
-    value = nnz_all * args.steps / (ms / 1e3)
-    e2e = nnz_all * args.steps / (ms_e2e / 1e3) if ms_e2e else None
+    nnz_all = int(over_ranks(X.nnz, world, "sum"))  # each rank's stream has its own seed
+    value = whole_job_rate(nnz_all, args.steps, ms)
+    e2e = whole_job_rate(nnz_all, args.steps, ms_e2e) if ms_e2e else None
     peak, peak_kind = peaks()
     per_launch_bytes = spmm_bytes / max(1, spmm_launches)
     per_launch_s = spmm_ms / 1e3 / max(1, spmm_launches)
