@@ -1,4 +1,4 @@
-"""Error measures and bounds used to judge sketches (oracle side).
+"""Error measures and bounds used to assess sketches (oracle side).
 
 Test infrastructure only (see the package docstring).
 
