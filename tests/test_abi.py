@@ -61,3 +61,24 @@ def test_null_context_is_rejected(lib):
     assert lib.sfd_sketch(None, None, 0) == sfd.SFD_EINVAL
     assert lib.sfd_merge(None, None) == sfd.SFD_EINVAL
     lib.sfd_destroy(None)
+
+
+def test_dense_product_forms_rejected_without_gpu(lib):
+    # argument checks that return before any CUDA call
+    assert lib.sfd_gram(10, 8, None, 8, None, 0) == sfd.SFD_EINVAL          # G null
+    p = 1  # a non-null dummy address: the checks below reject before using it
+    assert lib.sfd_gram(10, 8, p, 8, p, 3) == sfd.SFD_EINVAL               # no form 3
+    assert lib.sfd_gram(10, 136, p, 136, p, 2) == sfd.SFD_EINVAL           # tensor cores: k <= 128
+    assert lib.sfd_gemm_ts(10, 120, p, 120, p, 120, p, 120, 2) == sfd.SFD_EINVAL  # split: <= 112
+    assert lib.sfd_gemm_ts(10, 8, p, 4, p, 8, p, 8, 0) == sfd.SFD_EINVAL   # ldx < n
+
+
+def test_spmm_forms_without_gpu(lib):
+    assert lib.sfd_spmm_variant_count(0) == 2
+    assert lib.sfd_spmm_variant_count(1) == 3
+    p = 1
+    # variant out of range, fp16 needs k <= 128 and ld % 8 == 0
+    assert lib.sfd_csr_spmm_ex(4, 4, p, p, p, 4, p, 0, 4, p, 4, 0, 2) == sfd.SFD_EINVAL
+    assert lib.sfd_csr_spmm_ex(4, 4, p, p, p, 4, p, 1, 4, p, 4, 0, 0) == sfd.SFD_EINVAL
+    assert lib.sfd_csr_spmm_ex(4, 4, p, p, p, 136, p, 1, 136, p, 136, 0, 0) == sfd.SFD_EINVAL
+    assert lib.sfd_csr_spmm_ex(4, 4, p, p, p, 4, p, 0, 4, p, 4, 0, -1) == sfd.SFD_EINVAL
