@@ -1,5 +1,5 @@
 """The path at full workload sizes, in the launch configuration bench.py
-times (tensor-core form, three slots): the whole 1,000,000-row C2 stream
+times (tensor-core form, the default six slots): the whole 1,000,000-row C2 stream
 (d = 50,000, l = 100, 20 buffers) against properties that hold at any size,
 its first buffer against the FP64 oracle run on that buffer alone, C3's full
 width (d = 200,000, l = 200: the wide-block path), and the largest l."""
