@@ -59,7 +59,7 @@ def test_c2_full_stream_properties(lib, c2):
     s_k = spla.svds(A, k=k, tol=1e-4, return_singular_vectors=False)
     assert hi <= (fro2 - float((s_k ** 2).sum())) / (ell - k)   # FD bound
     # the same sketch with one slot (fixed reduction orders, buffers folded in
-    # order); at this size three concurrent slots have been seen to differ in
+    # order); at this size concurrent slots have been seen to differ in
     # rare runs (up to 1.5e-5 relative in B^T B, see the design notes), so the
     # check here is the 1e-4 parity bar, while the smaller streams are
     # checked bit for bit
