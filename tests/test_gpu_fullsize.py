@@ -60,7 +60,7 @@ def test_c2_full_stream_properties(lib, c2):
     assert hi <= (fro2 - float((s_k ** 2).sum())) / (ell - k)   # FD bound
     # the same sketch with one slot (fixed reduction orders, buffers folded in
     # order); at this size concurrent slots have been seen to differ in
-    # rare runs (up to 1.5e-5 relative in B^T B, see the design notes), so the
+    # rare runs (up to 1.5e-5 relative in B^T B; the cause is not found), so the
     # check here is the 1e-4 parity bar, while the smaller streams are
     # checked bit for bit
     s1 = lib.SFD(d, ell, 0, precision=1, slots=1)
