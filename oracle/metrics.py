@@ -3,6 +3,8 @@
 Test infrastructure only (see the package docstring).
 
 cov_err       ||A^T A - B^T B||_2 / ||A||_F^2            (Sec. 5, Measurements)
+cov_norm_psd  ||A^T A - B^T B||_2 when that matrix is PSD (Prop. 1: every FD /
+              SFD sketch), from its largest eigenvalue alone (large d)
 proj_err      ||A - pi_{B_k}(A)||_F^2 / ||A - A_k||_F^2  (Sec. 5, Measurements)
 tail_mass     ||A - A_k||_F^2                            (Sec. 1.1 notation)
 fd_bound      ||A - A_k||_F^2 / (l - k)                  (FD bound, Sec. 2)
@@ -41,6 +43,18 @@ def cov_norm(A, B, dense_limit=3000):
     """||A^T A - B^T B||_2."""
     lo, hi = residual_eigs(A, B, dense_limit)
     return max(abs(lo), abs(hi))
+
+
+def cov_norm_psd(A, B, tol=1e-6, seed=0):
+    """||A^T A - B^T B||_2 for a sketch B of A, whose residual A^T A - B^T B
+    is positive semi-definite (Prop. 1), so its 2-norm is its largest
+    eigenvalue: Lanczos on the operator from a seeded start vector."""
+    d = A.shape[1]
+    Bd = np.asarray(B, dtype=np.float64)
+    op = spla.LinearOperator((d, d), matvec=_gram_apply(A, Bd), dtype=np.float64)
+    v0 = np.random.default_rng(seed).standard_normal(d)
+    return float(spla.eigsh(op, k=1, which="LA", tol=tol, ncv=40, v0=v0, maxiter=20000,
+                            return_eigenvectors=False)[0])
 
 
 def fro2(A):

@@ -132,7 +132,14 @@ __device__ void tri_factor(const float* d, const float* e, float lam, float* U0,
     a_i = a_nx;
     c_i = c_nx;
   }
+  // the last row has no super-diagonals, multiplier or swap; they are written
+  // (not left as whatever the memory held) because the solve reads U1 and U2
+  // of that row times 0, and a leftover NaN / Inf pattern would make it NaN
   U0[(n - 1) * st] = a_i;
+  U1[(n - 1) * st] = 0.f;
+  U2[(n - 1) * st] = 0.f;
+  Lm[(n - 1) * st] = 0.f;
+  P[(n - 1) * st] = 0.f;
   for (int i = 0; i < n; ++i) {
     float u = U0[i * st];
     if (fabsf(u) < tiny_piv) U0[i * st] = u < 0.f ? -tiny_piv : tiny_piv;

@@ -135,3 +135,14 @@ def test_residual_eigs_sign_and_extremes():
     assert lo == pytest.approx(-3.0 * s[0] ** 2, rel=1e-10)
     assert hi == pytest.approx(s[1] ** 2, rel=1e-10)
     assert metrics.cov_norm(A, B) == pytest.approx(3.0 * s[0] ** 2, rel=1e-10)
+
+
+def test_cov_norm_psd_closed_form():
+    A, s, V = _known(50, 3500, SIGMA, 8)
+    As = sp.csr_matrix(A)
+    for k in (0, 2, 6):
+        B = s[:k, None] * V[:, :k].T if k else np.zeros((1, 3500))
+        assert metrics.cov_norm_psd(As, B) == pytest.approx(s[k] ** 2, rel=1e-8)
+    ell = 4
+    B = np.sqrt(s[:ell] ** 2 - s[ell - 1] ** 2)[:, None] * V[:, :ell].T
+    assert metrics.cov_norm_psd(As, B) == pytest.approx(s[ell - 1] ** 2, rel=1e-8)
