@@ -584,10 +584,14 @@ void build_work(Csr& c, cudaStream_t s) {
   int* slot_off = off + (n + 1);
   int* split_off = off + 2 * (n + 1);
   int* tmp = off + 3 * (n + 1);
-  w.d_n_items = item_off + n;
-  w.d_n_split = split_off + n;
+  // the item and split counts live at fixed places (counters[0], [1]), not at
+  // the end of offsets whose length follows the segment count: a CUDA graph
+  // captured for one buffer keeps the pointer and is replayed for buffers of
+  // other row counts
+  w.d_n_items = w.counters;
+  w.d_n_split = w.counters + 1;
   if (n <= 0) {
-    SFD_CUDA(cudaMemsetAsync(off, 0, 3 * sizeof(int), s));
+    SFD_CUDA(cudaMemsetAsync(w.counters, 0, 2 * sizeof(int), s));
     return;
   }
   // counts in split_seg/split_first/split_count scratch (filled after the scans)
@@ -603,6 +607,9 @@ void build_work(Csr& c, cudaStream_t s) {
                                                w.item_slot, w.item_split, w.split_seg,
                                                w.split_first, w.split_count);
   SFD_LAUNCH_CHECK();
+  SFD_CUDA(cudaMemcpyAsync(w.counters, item_off + n, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  SFD_CUDA(cudaMemcpyAsync(w.counters + 1, split_off + n, sizeof(int), cudaMemcpyDeviceToDevice,
+                           s));
 }
 
 void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float* partial,

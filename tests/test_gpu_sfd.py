@@ -212,3 +212,23 @@ def test_autotuning_never_changes_the_sketch(lib, precision):
     Bt, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, autotune=1)
     Bn, _ = _run_gpu(lib, X, d, ell, seed, precision=precision, autotune=0)
     assert np.array_equal(Bt, Bn)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_slot_reuse_with_buffers_of_other_row_counts(lib, precision):
+    # 3 full buffers of 2,000 rows and a flushed one of 1,000 on fewer slots
+    # than buffers: a slot's second buffer has another row count than its
+    # first, and its VerifySpectral (replayed from CUDA graphs captured on the
+    # first) must still see the right work-item count: no rejection, and the
+    # same bits as with a slot per buffer
+    d, ell, seed = 2000, 50, 9
+    X = synth.c1_gapped(seed=seed, n=7000)
+    outs = {}
+    for slots in (1, 2, 3, 6):
+        B, st = _run_gpu(lib, X, d, ell, seed, precision=precision, slots=slots)
+        assert st["buffers"] == 4 and st["vs_rejects"] == 0 and st["attempts"] == 4, (slots, st)
+        outs[slots] = B
+    assert all(np.array_equal(outs[6], outs[k]) for k in (1, 2, 3))
+    ref, o = O.sfd_stream(X.indptr, X.indices, X.values, d, ell, seed)
+    assert [e["attempts"] for e in o.log] == [1, 1, 1, 1]
+    assert metrics.bbt_rel_diff(outs[6], ref) <= (TOL_BBT if precision == 0 else 1e-3)
