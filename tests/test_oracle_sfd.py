@@ -268,15 +268,29 @@ def test_boosted_sparse_shrink_retry_and_keys():
     assert info["attempts"] == 2 and not info["verified"] and info["injected"] == 2
 
 
+def _step_spectrum_matrix(m=250, d=300, seed=0):
+    """l - 1 = 19 strong directions (sigma 10), one at sigma 4, 100 weak ones
+    (sigma 0.3), random orthonormal singular vectors. With q = 0 the start
+    block A'G often mixes the sigma-4 direction with the weak ones, so Z misses
+    most of it; the shrink by lambda_l^2 is then small and the missed direction
+    dominates the residual: ||A'^T A' - B'^T B'|| > Delta / 2."""
+    rng = np.random.default_rng(seed)
+    spec = np.concatenate([np.full(19, 10.0), [4.0], np.full(100, 0.3)])
+    U, _ = np.linalg.qr(rng.standard_normal((m, spec.size)))
+    V, _ = np.linalg.qr(rng.standard_normal((d, spec.size)))
+    return sp.csr_matrix((U * spec) @ V.T)
+
+
 def test_bssh_catches_a_failed_shrink():
-    # q = 0 on a slowly decaying spectrum misses directions; VS must reject those runs
-    # whose residual norm exceeds Delta, and accept those within Delta/2 (Lemma 4.1)
-    rng = np.random.default_rng(12)
-    m, d, ell = 200, 150, 12
-    A = sp.csr_matrix(rng.standard_normal((m, d)) * (0.97 ** np.arange(d))[None, :])
+    # q = 0 on a spectrum with a step at l: some runs miss the l-th direction.
+    # Lemma 4.1: VS accepts every run whose residual norm is within Delta/2
+    # (deterministically) and rejects those at or above Delta (w.h.p.)
+    A = _step_spectrum_matrix()
     Ad = A.toarray()
-    seen = {True: 0, False: 0}
-    for s in range(20):
+    m, d = Ad.shape
+    ell = 20
+    seen = {"accept_small": 0, "reject_large": 0, "accept_large": 0}
+    for s in range(24):
         Bp, _ = O.sparse_shrink(A, ell, 0, philox.gaussian_G(s, 0, 0, d, ell))
         Delta = ((Ad ** 2).sum() - (Bp ** 2).sum()) / (O.ALPHA * ell)
         nrm = np.linalg.eigvalsh(Ad.T @ Ad - bbt(Bp))[-1]
@@ -284,9 +298,15 @@ def test_bssh_catches_a_failed_shrink():
                                   O.vs_steps(d, 1e-3))
         if nrm <= Delta / 2:
             assert ok
+            seen["accept_small"] += 1
         if nrm >= Delta:
-            seen[ok] += 1
-    assert seen[True] <= 1
+            seen["reject_large" if not ok else "accept_large"] += 1
+    assert seen["accept_small"] >= 3 and seen["reject_large"] >= 3, seen
+    assert seen["accept_large"] <= 1, seen
+    # and BoostedSparseShrink retries such a buffer until VS accepts
+    _, info = O.boosted_sparse_shrink(A, ell, 0.01, 0, 0, 0)
+    assert info["verified"] and info["attempts"] >= 2
+    assert all(h["logsum"] > 0 for h in info["history"][:-1])
 
 
 # ----------------------------------------------------------------------------
