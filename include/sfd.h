@@ -157,6 +157,27 @@ int sfd_sketch(sfd_ctx* ctx, float* B_out, int where);
  * Requires equal d and l and the same device. */
 int sfd_merge(sfd_ctx* dst, sfd_ctx* src);
 
+/* Checkpoint (no counterpart in the paper; the stream state of Alg. 2 between
+ * rows is the sketch B, the open buffer A' and the buffer counter b). sfd_save
+ * writes the context's state to `buf` (host memory, `cap` bytes) and its size
+ * to *size_out; buf = NULL only reports the size. Nothing is flushed: the
+ * state is taken as it stands after the last call (every call leaves no
+ * buffer in flight). The blob holds d, l, seed, b, the options that decide
+ * the result (delta, verify, c_q, q_override, retry_cap, precision, q_mode,
+ * strict, q_margin, q_tau), the counters, B (l x d float32), the open buffer
+ * (int32 row pointer, int32 columns, float32 values), the learned-q network
+ * when one is set (not the q_mode 2 label log), and an FNV-1a hash; host
+ * byte order. Errors: SFD_EINVAL (cap too small), SFD_ENOMEM, SFD_ECUDA. */
+int sfd_save(sfd_ctx* ctx, void* buf, int64_t cap, int64_t* size_out);
+
+/* A new context on the current device from a blob of sfd_save: appending the
+ * same rows to it gives the same sketch, bit for bit, as appending them to the
+ * saved context. The computing options come from the blob; `runtime`
+ * (nullable) supplies only cuda_stream, slots, profile and autotune.
+ * Errors: SFD_EINVAL (bad size, magic, version, hash or contents), SFD_ENOMEM,
+ * SFD_ECUDA. */
+int sfd_load(const void* buf, int64_t size, const sfd_options* runtime, sfd_ctx** out);
+
 /* Counters; see sfd_stats. */
 int sfd_get_stats(const sfd_ctx* ctx, sfd_stats* out);
 
@@ -312,14 +333,20 @@ int sfd_symeig(int32_t n, const float* S, int32_t nwant, float* evals, float* ev
  * allocate device memory: a process whose caching allocator already holds the
  * device's memory budget, or a latency-critical loop that cannot take the
  * device-wide synchronisation cudaMalloc / cudaFree may cause. Its scratch is
- * a fixed array inside libsfd.so (~2.1 MB, held on every GPU that loads the
- * library until the process exits), so n <= 256 (1 <= nwant <= n); larger n
- * returns SFD_EINVAL. S, evals, evecs are caller-owned device memory as in
- * sfd_symeig. Runs on the legacy default stream (0) of the current device and
- * returns after that stream has finished. The first call on each device looks
- * up the array's device address; make that first call before any stream
- * capture. All calls share the one array: calls that overlap on the GPU (from
- * several host threads or streams) race and must be serialised by the caller.
+ * a fixed array inside libsfd.so (~2.1 MB), so n <= 256 (1 <= nwant <= n);
+ * larger n returns SFD_EINVAL. S, evals, evecs are caller-owned device memory
+ * as in sfd_symeig. Runs on the legacy default stream (0) of the current
+ * device and returns after that stream has finished.
+ * The first call on each device (and again after the device's context was
+ * reset) loads the part of the library that holds the array and looks up its
+ * device address: with CUDA's lazy module loading (the default) that first
+ * call is when the array (~2.1 MB) and that code take device memory, and it
+ * may synchronise the device. Make one warm-up call per device before handing
+ * the memory budget to an allocator and before any stream capture; from then
+ * on calls allocate nothing and the device holds the array until its context
+ * ends. All calls share the one array, which keeps the last call's contents:
+ * calls that overlap on the GPU (from several host threads or streams) race
+ * and must be serialised by the caller.
  * Errors: SFD_EINVAL, SFD_ECUDA. */
 int sfd_symeig_noalloc(int32_t n, const float* S, int32_t nwant, float* evals, float* evecs);
 

@@ -57,7 +57,7 @@ EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "s
            "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_q_model", "sfd_q_log",
            "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train", "sfd_batch_create",
            "sfd_batch_append", "sfd_batch_wait", "sfd_batch_sketch", "sfd_batch_merge_tree",
-           "sfd_batch_stats", "sfd_batch_destroy"]
+           "sfd_batch_stats", "sfd_batch_destroy", "sfd_save", "sfd_load"]
 QF, QPARAMS = 16, 5313
 
 _lib = None
@@ -113,6 +113,8 @@ def load(path=None):
     L.sfd_batch_merge_tree.argtypes = [vp, vp, ctypes.c_int]
     L.sfd_batch_stats.argtypes = [vp, i32, ctypes.POINTER(sfd_stats)]
     L.sfd_batch_destroy.argtypes = [vp]
+    L.sfd_save.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.sfd_load.argtypes = [vp, i64, ctypes.POINTER(sfd_options), ctypes.POINTER(vp)]
     for name in EXPORTS:
         fn = getattr(L, name)
         if name not in ("sfd_options_init", "sfd_destroy", "sfd_strerror", "sfd_last_error",
@@ -210,6 +212,25 @@ def sfd_reset(ctx):
 
 def sfd_destroy(ctx):
     load().sfd_destroy(ctx)
+
+
+def sfd_save(ctx):
+    """The context's state as bytes (sfd_save): sketch, open buffer, counters."""
+    n = ctypes.c_int64()
+    _check(load().sfd_save(ctx, None, 0, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().sfd_save(ctx, buf, n.value, ctypes.byref(n)), ctx)
+    return buf.raw[:n.value]
+
+
+def sfd_load(blob, runtime=None):
+    """A context resumed from sfd_save bytes; `runtime` options supply only
+    cuda_stream, slots, profile and autotune."""
+    h = ctypes.c_void_p()
+    b = bytes(blob)
+    _check(load().sfd_load(b, len(b), ctypes.byref(runtime) if runtime is not None else None,
+                           ctypes.byref(h)))
+    return h
 
 
 def sfd_bssh_buffer(m, d, ell, rowptr, colidx, vals, seed, b, Bp_out, opts=None):
@@ -356,6 +377,21 @@ class SFD:
 
     def stats(self):
         return sfd_get_stats(self.ctx)
+
+    def save(self):
+        """Checkpoint: bytes that sfd_load / SFD.load turn back into this stream."""
+        return sfd_save(self.ctx)
+
+    @classmethod
+    def load(cls, blob, **runtime):
+        """Resume a stream from SFD.save bytes (same d, l, seed, options)."""
+        import struct
+        d, ell = struct.unpack_from("<qi", blob, 16)
+        self = cls.__new__(cls)
+        self.d, self.ell = int(d), int(ell)
+        self._opts = options(**runtime) if runtime else None
+        self.ctx = sfd_load(blob, self._opts)
+        return self
 
     def set_q_model(self, params):
         P = None if params is None else _f32(params, QPARAMS)
