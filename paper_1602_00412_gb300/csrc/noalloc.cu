@@ -6,9 +6,18 @@
 // nothing left for a private allocation, and a latency-critical loop cannot
 // absorb the device-wide synchronisation that cudaMalloc / cudaFree may
 // perform. This entry point allocates nothing: the caller passes the input and
-// the outputs, and the scratch is `g_symeig_scratch`, a file-scope array that
-// every GPU which loads the library holds until the process exits.
-#include <atomic>
+// the outputs, and the scratch is `g_symeig_scratch`, a file-scope array.
+//
+// When the array takes device memory: with CUDA's lazy module loading (the
+// default), the module that holds it is loaded into a context on the first
+// call that needs its device address, so the first call on each device
+// reserves the array (~2.1 MB) and the module's code there and may
+// synchronise; from then on the device holds it until the context ends.
+// Callers that must not see that make one warm-up call per device before they
+// hand the memory budget to their allocator and before any stream capture.
+#include <cuda.h>
+
+#include <mutex>
 
 #include "sfd_internal.cuh"
 
@@ -27,10 +36,62 @@ constexpr size_t kNoAllocFloats = (size_t)kNoAllocMaxN * kNoAllocMaxN + kNoAlloc
 
 static __device__ __align__(256) float g_symeig_scratch[kNoAllocFloats];
 
-// Device address of g_symeig_scratch, looked up once per device. In host code
-// the symbol name is only a host-side stand-in, never a device address.
+// The array's device address per device, tagged with the id of the context it
+// was resolved in. In host code the symbol name is only a host-side stand-in,
+// never a device address; and an address is valid only in its own context (a
+// cudaDeviceReset ends the primary context, and the module is loaded afresh
+// in the next one), so the cache is keyed on the context id, which CUDA never
+// reuses within a process.
 constexpr int kMaxDevices = 64;
-std::atomic<float*> g_scratch_addr[kMaxDevices];
+struct Resolved {
+  unsigned long long ctx_id = 0;
+  float* addr = nullptr;
+};
+Resolved g_resolved[kMaxDevices];
+std::mutex g_mu;
+
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context (0 when there is none).
+bool current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrent get_current = nullptr;
+  static CtxGetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) !=
+            cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+      return false;
+    get_current = reinterpret_cast<CtxGetCurrent>(a);
+    get_id = reinterpret_cast<CtxGetId>(b);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return false;
+  *id = 0;
+  return !ctx || get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_symeig_scratch in the current context of device `dev`,
+// resolved by cudaGetSymbolAddress once per device and context (with that
+// device current; the first resolution loads the module).
+float* scratch_address(int dev) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  unsigned long long id = 0;
+  if (!current_ctx_id(&id)) return nullptr;
+  Resolved& r = g_resolved[dev];
+  if (id != 0 && r.addr && r.ctx_id == id) return r.addr;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_symeig_scratch) != cudaSuccess || !p) return nullptr;
+  if (!current_ctx_id(&id) || id == 0) return nullptr;  // the lookup made the context current
+  r.ctx_id = id;
+  r.addr = static_cast<float*>(p);
+  return r.addr;
+}
 
 }  // namespace
 }  // namespace sfd
@@ -43,14 +104,8 @@ extern "C" int sfd_symeig_noalloc(int32_t n, const float* S, int32_t nwant, floa
   if (symeig_work_floats(n, nwant) > kNoAllocFloats) return SFD_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SFD_ECUDA;
-  float* scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
-  if (!scratch) {
-    // first call on this device: resolve the array's device address
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_symeig_scratch) != cudaSuccess || !p) return SFD_ECUDA;
-    scratch = static_cast<float*>(p);
-    g_scratch_addr[dev].store(scratch, std::memory_order_release);
-  }
+  float* scratch = scratch_address(dev);
+  if (!scratch) return SFD_ECUDA;
   try {
     // the eigensolver writes every scratch word before reading it, so nothing
     // needs clearing between calls
