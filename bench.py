@@ -15,7 +15,8 @@ same call sequence from pinned host buffers (host->device copy of the stream
 and device->host copy of the sketch inside the timed region).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-stream (the first 10,000 rows: one flushed buffer through BSSh + DSh).
+stream: its first 50,000 rows, i.e. the first buffer exactly as the stream
+closes it (m = d = 50,000, q = 13), through BSSh + DSh.
 """
 import argparse
 import hashlib
@@ -35,7 +36,7 @@ WORKLOAD = dict(name="c2", n=1_000_000, d=50_000, ell=100, k=20, mu=50, zipf=1.1
 DESC = ("SFD stream n=1,000,000 d=50,000 l=100, nnz/row~Poisson(50), Zipf(1.1) columns, "
         "planted rank-20 (10*0.8^t) + 0.1 N(0,1), fp32 CSR")
 METRIC = "SFD input nnz/sec at fixed cov-error"
-REF_SAMPLE_ROWS = 10_000
+REF_SAMPLE_ROWS = 50_000   # one whole buffer of the stream (rows = d)
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the cov-err evaluation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="time only the chosen form (not the plain FP32 and verify-off forms)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="0: FP32 throughout; 1: tensor-core (TF32) Gram and X R^-1 in the "
                          "orthonormalisations of all but the last power iteration")
@@ -210,57 +213,180 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes per launch of the SpMM stage (dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the stage's launches of one ncu capture),
+# valid while csrc/k_sparse.cu hashes to the key; the ncu summary in profiles/
+# gives the command and the per-kernel figures.
+SPMM_TRAFFIC = {"53b6a74b6f9f59e0": 33.87e6, "bbaa904771a301f8": 33.87e6}
+
+
 def traffic_record():
-    """DRAM bytes per launch of the SpMM stage from the committed ncu summary
-    (profiles/spmm_c2_traffic.md, lines "source_sha <hex>" and
-    "dram_bytes_per_launch <n>"), valid only while the kernel source is
-    unchanged; None otherwise."""
-    p = os.path.join(ROOT, "profiles", "spmm_c2_traffic.md")
-    rec = {}
-    try:
-        with open(p) as f:
-            for line in f:
-                parts = line.strip().strip("`").split()
-                if len(parts) == 2 and parts[0] in ("source_sha", "dram_bytes_per_launch"):
-                    rec[parts[0]] = parts[1]
-    except OSError:
-        return None
+    """DRAM bytes per SpMM-stage launch for the current sparse-kernel source,
+    or None when the kernels changed since the counters were taken."""
     src = os.path.join(ROOT, "paper_1602_00412_gb300", "csrc", "k_sparse.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h or "dram_bytes_per_launch" not in rec:
+    return SPMM_TRAFFIC.get(h)
+
+
+def oracle_golden(rows, seed):
+    """The FP64 oracle's cov-err on this stream, stored by
+    tests/golden/make_c2_oracle.py (only for the full stream of seed 0)."""
+    p = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
+    try:
+        with open(p) as f:
+            g = json.load(f)
+    except (OSError, ValueError):
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return g if (g.get("rows") == rows and g.get("seed") == seed) else None
 
 
 # ------------------------------------------------------------------ arms
+def ref_sample_rows(steps, warmup):
+    """Rows of the stream one reference step runs: the stream's first buffer
+    (50,000 rows, ~10-25 s of CPU) while the whole run stays within a few
+    minutes (about 8 such samples), else a proportionally shorter prefix
+    (one flushed buffer of fewer rows)."""
+    n = steps + warmup
+    if n <= 8:
+        return REF_SAMPLE_ROWS
+    return max(10_000, (REF_SAMPLE_ROWS * 8 // n) // 1000 * 1000)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
+    rows = ref_sample_rows(args.steps, args.warmup)
     times, nnz = [], 0
     for i in range(args.warmup + args.steps):
-        sec, nnz = run_oracle_sample(REF_SAMPLE_ROWS, 0, threads)
+        sec, nnz = run_oracle_sample(rows, 0, threads)
         if i >= args.warmup:
             times.append(sec)
     tot = sum(times)
     val = nnz * len(times) / tot
-    sample = "first %d rows of the c2 stream (%d nnz): one flushed buffer, BSSh + DSh in FP64" % (
-        REF_SAMPLE_ROWS, nnz)
+    sample = ("first %d rows of the c2 stream (%d nnz) through BSSh + DSh in FP64 (%s)" % (
+        rows, nnz, "its first buffer, m = d, q = 13" if rows == REF_SAMPLE_ROWS
+        else "one flushed buffer of %d rows" % rows))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "nnz/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": DESC, "sample_rows": REF_SAMPLE_ROWS},
+            "config": {"workload": DESC, "sample_rows": rows},
             "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ our arm
+def train_q_model(sfd, args, d, ell):
+    """Labelled streams of other seeds (q_mode 2), then Adam on the GPU."""
+    import numpy as np
+    t0 = time.time()
+    feats, labels = [], []
+    for s in range(args.train_streams):
+        Xt = make_stream(args.train_rows, 1000 + s)
+        tc = sfd.SFD(d, ell, 1000 + s, q_mode=2, precision=args.precision, slots=args.slots)
+        tc.append(Xt.indptr, Xt.indices, Xt.values)
+        tc.sketch()
+        F, L, _ = tc.q_log()
+        tc.close()
+        feats.append(F)
+        labels.append(L)
+    F, L = np.concatenate(feats), np.concatenate(labels)
+    theta, loss = sfd.sfd_q_train(F, L, sfd.q_init_params(0), epochs=300, batch=8, lr=3e-3)
+    info = {"train_buffers": int(len(L)), "labels": sorted(set(int(x) for x in L)),
+            "train_loss": loss, "train_s": round(time.time() - t0, 1),
+            "train_streams": "%d x %d rows, seeds 1000+" % (args.train_streams, args.train_rows)}
+    return theta, info
+
+
+class Form:
+    """One form of the path timed on the same stream: `value` with the stream
+    resident in HBM, `e2e` from pinned host buffers (H2D of the stream and D2H
+    of the sketch inside the timed region)."""
+
+    def __init__(self, name, **opts):
+        self.name, self.opts = name, opts
+        self.ms = self.ms_e2e = None
+        self.stats, self.clocks, self.B = None, None, None
+
+
+def time_form(form, sfd, io, args, world, stream, theta=None, clocks_index=None, e2e=True):
+    import torch
+    import torch.distributed as dist
+    d, ell, rank = io["d"], io["ell"], io["rank"]
+    ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, slots=args.slots,
+                  q_margin=args.q_margin, **form.opts)
+    if form.opts.get("q_mode") == 1:
+        ctx.set_q_model(theta)
+
+    def step_device():
+        ctx.reset()
+        ctx.append(io["ip_d"], io["ix_d"], io["vv_d"])
+        ctx.sketch(io["B_d"])
+
+    def step_host():
+        ctx.reset()
+        ctx.append(io["ip_h"], io["ix_h"], io["vv_h"])
+        ctx.sketch(io["B_h"])
+
+    def timed(fn, steps):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return over_ranks(e0.elapsed_time(e1), world, "max")
+
+    for _ in range(args.warmup):
+        step_device()
+    clk = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clk:
+        clk.start()
+    form.ms = timed(step_device, args.steps)
+    form.stats = ctx.stats()          # counters of the last timed step (each step resets)
+    if clk:
+        form.clocks = clk.stop()
+    form.B = io["B_d"].cpu().numpy()
+    if e2e:
+        for _ in range(max(1, args.warmup // 3)):
+            step_host()
+        form.ms_e2e = timed(step_host, args.steps)
+    ctx.close()
+    return form
+
+
+def spmm_roofline_one_slot(sfd, io, args, stream, peak):
+    """The SpMM stage's own duration: the stream once more with one buffer in
+    flight (slots = 1), every sparse-product launch timed by CUDA events on
+    the stream it runs on; there it shares the GPU only with the merge
+    stream's DenseShrink."""
+    import torch
+    iso = sfd.SFD(io["d"], io["ell"], io["rank"], cuda_stream=stream.cuda_stream, profile=1,
+                  precision=args.precision, slots=1)
+    iso.append(io["ip_d"], io["ix_d"], io["vv_d"])
+    iso.sketch(io["B_d"])
+    torch.cuda.synchronize()
+    st = iso.stats()
+    iso.close()
+    if not st["spmm_launches"]:
+        return None
+    per_bytes = st["spmm_bytes"] / st["spmm_launches"]
+    per_s = st["spmm_ms"] / 1e3 / st["spmm_launches"]
+    return {"achieved": per_bytes / per_s / 1e9, "launches": st["spmm_launches"],
+            "bytes_per_launch": per_bytes, "avg_launch_us": per_s * 1e6}
+
+
 def ours_arm(args, rank, world, local):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     torch.cuda.set_device(local)
     from paper_1602_00412_gb300.build import build
@@ -271,156 +397,105 @@ def ours_arm(args, rank, world, local):
     w = WORKLOAD
     d, ell = w["d"], w["ell"]
     stream = torch.cuda.current_stream()
-    # device-resident inputs
-    ip_d = torch.from_numpy(X.indptr).cuda()
-    ix_d = torch.from_numpy(X.indices).cuda()
-    vv_d = torch.from_numpy(X.values).cuda()
-    B_d = torch.empty((ell, d), device="cuda")
-    # pinned host inputs for e2e
-    ip_h = torch.from_numpy(X.indptr).pin_memory().numpy()
-    ix_h = torch.from_numpy(X.indices).pin_memory().numpy()
-    vv_h = torch.from_numpy(X.values).pin_memory().numpy()
-    B_h = torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()
-    qinfo = None
+    io = {"d": d, "ell": ell, "rank": rank,
+          "ip_d": torch.from_numpy(X.indptr).cuda(), "ix_d": torch.from_numpy(X.indices).cuda(),
+          "vv_d": torch.from_numpy(X.values).cuda(), "B_d": torch.empty((ell, d), device="cuda"),
+          "ip_h": torch.from_numpy(X.indptr).pin_memory().numpy(),
+          "ix_h": torch.from_numpy(X.indices).pin_memory().numpy(),
+          "vv_h": torch.from_numpy(X.values).pin_memory().numpy(),
+          "B_h": torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()}
+    theta, qinfo = (None, None)
     if args.q_mode == "learned":
-        t0 = time.time()
-        feats, labels = [], []
-        for s in range(args.train_streams):
-            Xt = make_stream(args.train_rows, 1000 + s)
-            tc = sfd.SFD(d, ell, 1000 + s, q_mode=2, precision=args.precision, slots=args.slots)
-            tc.append(Xt.indptr, Xt.indices, Xt.values)
-            tc.sketch()
-            F, L, _ = tc.q_log()
-            tc.close()
-            feats.append(F)
-            labels.append(L)
-        F, L = np.concatenate(feats), np.concatenate(labels)
-        theta, loss = sfd.sfd_q_train(F, L, sfd.q_init_params(0), epochs=300, batch=8, lr=3e-3)
-        qinfo = {"train_buffers": int(len(L)), "labels": sorted(set(int(x) for x in L)),
-                 "train_loss": loss, "train_s": round(time.time() - t0, 1),
-                 "train_streams": "%d x %d rows, seeds 1000+" % (args.train_streams, args.train_rows)}
-    ctx = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1,
-                  precision=args.precision, slots=args.slots,
-                  q_mode=1 if args.q_mode == "learned" else 0, q_margin=args.q_margin)
-    if args.q_mode == "learned":
-        ctx.set_q_model(theta)
-
-    def step_device():
-        ctx.reset()
-        ctx.append(ip_d, ix_d, vv_d)
-        ctx.sketch(B_d)
-
-    def step_host():
-        ctx.reset()
-        ctx.append(ip_h, ix_h, vv_h)
-        ctx.sketch(B_h)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def timed(fn, steps):
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        return over_ranks(e0.elapsed_time(e1), world, "max")
-
-    for _ in range(args.warmup):
-        step_device()
-    clk = ClockSampler(local)
-    clk.start()
-    ms = timed(step_device, args.steps)
-    # counters cover the last timed step (every step starts with a reset)
-    st = ctx.stats()
-    clocks = clk.stop()
-    spmm_launches, spmm_ms, spmm_bytes = st["spmm_launches"], st["spmm_ms"], st["spmm_bytes"]
-    ms_e2e = None
-    if not args.no_e2e:
-        for _ in range(max(1, args.warmup // 3)):
-            step_host()
-        ms_e2e = timed(step_host, args.steps)
-    B = B_d.cpu().numpy()
-    nnz_all = int(over_ranks(X.nnz, world, "sum"))  # each rank's stream has its own seed
-    value = whole_job_rate(nnz_all, args.steps, ms)
-    e2e = whole_job_rate(nnz_all, args.steps, ms_e2e) if ms_e2e else None
+        theta, qinfo = train_q_model(sfd, args, d, ell)
+    learned = args.q_mode == "learned"
+    chosen = Form("chosen", precision=args.precision, q_mode=1 if learned else 0, profile=1)
+    time_form(chosen, sfd, io, args, world, stream, theta, clocks_index=local, e2e=not args.no_e2e)
+    forms = [chosen]
+    if not args.no_forms:
+        # the plain FP32 path (fixed schedule), and SparseShrink without
+        # VerifySpectral as in the paper's experiments (Sec. 5)
+        if args.precision != 0 or learned:
+            forms.append(time_form(Form("plain", precision=0), sfd, io, args, world, stream,
+                                   e2e=not args.no_e2e))
+        forms.append(time_form(Form("verify_off", precision=args.precision, verify=0,
+                                    q_mode=1 if learned else 0), sfd, io, args, world, stream,
+                               theta, e2e=False))
+    nnz_all = int(over_ranks(X.nnz, world, "sum"))   # each rank's stream has its own seed
+    rate = lambda ms: whole_job_rate(nnz_all, args.steps, ms) if ms else None
+    st = chosen.stats
     peak, peak_kind = peaks()
-    per_launch_bytes = spmm_bytes / max(1, spmm_launches)
-    per_launch_s = spmm_ms / 1e3 / max(1, spmm_launches)
-    achieved = per_launch_bytes / per_launch_s / 1e9 if spmm_launches else None
-    out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None,
+    contended = None
+    if st["spmm_launches"]:
+        per_s = st["spmm_ms"] / 1e3 / st["spmm_launches"]
+        contended = {"achieved": st["spmm_bytes"] / st["spmm_launches"] / per_s / 1e9,
+                     "avg_launch_us": per_s * 1e6, "launches_per_step": st["spmm_launches"]}
+    iso = spmm_roofline_one_slot(sfd, io, args, stream, peak)
+    roof = {"kernel": "SpMM stage: k_spmm_h (fp16 blocks) / k_spmm (fp32) for A'X (CSR) and "
+                      "A'^T Y (CSC), incl. split fix-up; duration from the one-slot run",
+            "bound": "hbm", "achieved": iso["achieved"] if iso else None, "peak": peak,
+            "unit": "GB/s", "frac": (iso["achieved"] / peak) if iso else None,
+            "peak_kind": "of %s" % peak_kind, "traffic": traffic_record(),
+            "algorithmic_bytes_per_launch": iso["bytes_per_launch"] if iso else None,
+            "avg_launch_us": iso["avg_launch_us"] if iso else None,
+            "achieved_contended": contended["achieved"] if contended else None,
+            "frac_contended": contended["achieved"] / peak if contended else None,
+            "avg_launch_us_contended": contended["avg_launch_us"] if contended else None,
+            "launches_per_step": st["spmm_launches"]}
+    out = {"metric": METRIC, "value": rate(chosen.ms), "unit": "nnz/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": chosen.ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == 0 else "tf32+f32", "data": "synthetic",
            "config": {"workload": DESC, "rows": X.n, "d": d, "ell": ell, "nnz_per_rank": X.nnz,
                       "precision": ["fp32", "mixed-tf32"][args.precision],
                       "q_mode": args.q_mode, "q_model": qinfo,
-                      "q_margin": args.q_margin if args.q_mode == "learned" else None,
+                      "q_margin": args.q_margin if learned else None,
                       "buffers_per_step": st["buffers"], "attempts_per_step": st["attempts"],
                       "q_per_attempt": st["q_total"] / max(1, st["attempts"]),
                       "l2": "inputs larger than L2 (CSR stream %.0f MB per rank)" % (
                           (X.indptr.nbytes + X.indices.nbytes + X.values.nbytes) / 1e6),
                       "parallelism": "independent streams per GPU (weak)" if world > 1 else "1 GPU"},
-           "rows_per_s": X.n * world * args.steps / (ms / 1e3),
-           "e2e": {"value": e2e, "unit": "nnz/s",
+           "rows_per_s": X.n * world * args.steps / (chosen.ms / 1e3),
+           "e2e": {"value": rate(chosen.ms_e2e), "unit": "nnz/s",
                    "h2d_bytes_per_step": int(X.indptr.nbytes + X.indices.nbytes + X.values.nbytes),
-                   "d2h_bytes_per_step": int(B_h.nbytes)},
-           "roofline": {"kernel": "SpMM stage: k_spmm_h (fp16 blocks) / k_spmm (fp32) for A'X (CSR) "
-                                  "and A'^T Y (CSC), incl. split fix-up",
-                        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": (achieved / peak) if achieved else None,
-                        "peak_kind": "of %s" % peak_kind,
-                        "traffic": traffic_record(), "launches_per_step": spmm_launches,
-                        "algorithmic_bytes_per_launch": per_launch_bytes,
-                        "avg_launch_us": per_launch_s * 1e6},
+                   "d2h_bytes_per_step": int(io["B_h"].nbytes)},
+           "roofline": roof,
            "gpu_launches": int(st["kernel_launches"]) * args.steps,
            "gpu_launches_per_step": int(st["kernel_launches"]),
-           "clocks": clocks}
-    # the SpMM roofline once more with one buffer in flight (slots = 1): the
-    # launches then share the GPU only with the merge stream's DenseShrink, so
-    # their event times are close to the kernel's own duration
-    iso = sfd.SFD(d, ell, rank, cuda_stream=stream.cuda_stream, profile=1,
-                  precision=args.precision, slots=1)
-    iso.append(ip_d, ix_d, vv_d)
-    iso.sketch(B_d)
-    torch.cuda.synchronize()
-    sti = iso.stats()
-    iso.close()
-    if sti["spmm_launches"]:
-        a_iso = sti["spmm_bytes"] / sti["spmm_launches"] / (sti["spmm_ms"] / 1e3 / sti["spmm_launches"]) / 1e9
-        out["roofline"]["achieved_one_slot"] = a_iso
-        out["roofline"]["frac_one_slot"] = a_iso / peak
-        out["roofline"]["avg_launch_us_one_slot"] = sti["spmm_ms"] * 1e3 / sti["spmm_launches"]
+           "clocks": chosen.clocks}
+    out["forms"] = {f.name: {"value": rate(f.ms), "e2e": rate(f.ms_e2e),
+                             "ms_per_step": f.ms / args.steps,
+                             "attempts_per_step": f.stats["attempts"],
+                             "vs_rejects_per_step": f.stats["vs_rejects"],
+                             "options": {k: v for k, v in f.opts.items() if k != "profile"}}
+                    for f in forms}
+    if "plain" in out["forms"]:
+        out["plain"] = dict(out["forms"]["plain"])
+        out["plain"]["chosen_over_plain"] = out["value"] / out["plain"]["value"]
     if rank == 0 and not args.no_check:
-        out["accuracy"] = cov_err_check(X, B, w["k"])
-        out["accuracy"]["within_fd_bound"] = out["accuracy"]["cov_norm"] <= out["accuracy"]["fd_bound"]
-        if args.q_mode != "fixed" or args.precision != 0:
-            # the same stream through the plain path (fp32, fixed q), untimed:
-            # the chosen form must keep cov-err within 2% of it
-            ref = sfd.SFD(d, ell, rank, precision=0)
-            ref.append(X.indptr, X.indices, X.values)
-            Bp = ref.sketch()
-            ref.close()
-            acc_p = cov_err_check(X, Bp, w["k"])
-            out["accuracy"]["cov_err_plain"] = acc_p["cov_err"]
-            out["accuracy"]["rel_to_plain"] = out["accuracy"]["cov_err"] / acc_p["cov_err"] - 1.0
+        g = oracle_golden(X.n, rank)
+        acc = {}
+        for f in forms:
+            a = cov_err_check(X, f.B, w["k"])
+            a["within_fd_bound"] = a["cov_norm"] <= a["fd_bound"]
+            if g:
+                a["cov_err_oracle"] = g["cov_err"]
+                a["rel_to_oracle"] = a["cov_err"] / g["cov_err"] - 1.0
+                a["within_2pct_of_oracle"] = abs(a["rel_to_oracle"]) <= 0.02
+            acc[f.name] = a
+        out["accuracy"] = dict(acc["chosen"])
+        out["accuracy"]["forms"] = {k: v for k, v in acc.items() if k != "chosen"}
+        out["accuracy"]["oracle"] = ("tests/golden/c2_oracle.json: FP64 oracle on the same stream"
+                                     if g else "no stored oracle value for this stream")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         sec, nnz = run_oracle_sample(REF_SAMPLE_ROWS, 0, threads)
         out["cpu_baseline"] = {"value": nnz / sec, "unit": "nnz/s", "cores": threads,
                                "kind": "oracle",
-                               "sample": "first %d rows (%d nnz) of the stream: one flushed "
-                                         "buffer through BSSh + DSh, FP64 numpy/scipy" % (
-                                             REF_SAMPLE_ROWS, nnz)}
-    ctx.close()
+                               "sample": "first %d rows (%d nnz) of the stream: its first buffer "
+                                         "(m = d, q = 13) through BSSh + DSh, FP64 numpy/scipy, "
+                                         "BLAS threads = host cores" % (REF_SAMPLE_ROWS, nnz)}
     if rank == 0:
         print(json.dumps(out), flush=True)
-
 
 def main():
     args = parse()
