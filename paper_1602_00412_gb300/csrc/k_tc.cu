@@ -275,6 +275,167 @@ __global__ void __launch_bounds__(kTcThreads)
   if (warp == 0) tmem_free(tmem, 128);
 }
 
+// ------------------------------------------------------ Gram, bulk copies
+// The same partial Grams as k_tc_gram for a block whose rows start on 16-byte
+// boundaries (ldx % 4 == 0, X 16-byte aligned), so that the kGK rows of a
+// stage are one contiguous run of memory: thread 0 moves each stage with a
+// single bulk copy (the TMA engine, cp.async.bulk with an mbarrier completing
+// on the byte count) into a ring of kBR raw stages, kept kBR - 1 stages
+// ahead. Each thread then transposes its column of a landed stage into the
+// K-major core layout of the MMA ring (two buffers, reused once the MMAs that
+// read them have completed), so the per-element copies of k_tc_gram become
+// one instruction per stage plus shared-memory moves.
+constexpr int kBR = 6;  // raw stages in flight
+template <bool SPLIT>
+struct GramBulk {
+  static constexpr int Raw = kGK * 128;                          // floats per raw stage (ldx <= 128)
+  static constexpr int Core = kGTile * (SPLIT ? 2 : 1);          // floats per MMA buffer
+  static constexpr int Smem = (kBR * Raw + 2 * Core) * (int)sizeof(float);  // 128 / 160 KB
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes));
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kTcThreads)
+    k_tc_gram_bulk(const float* __restrict__ X, int ldx, int n, int64_t rows,
+                   int64_t rows_per_chunk, float* __restrict__ partial, int* __restrict__ flags) {
+  using G = GramBulk<SPLIT>;
+  extern __shared__ __align__(1024) float smem[];
+  float* raw = smem;                  // kBR x (kGK x ldx), row-major as in memory
+  float* core = smem + kBR * G::Raw;  // 2 MMA buffers: hi (and lo)
+  __shared__ __align__(8) uint64_t full[kBR];   // raw stage landed
+  __shared__ __align__(8) uint64_t mmad[2];     // MMAs of a core buffer done
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tmem_alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    for (int b = 0; b < kBR; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[b])), "r"(1));
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mmad[b])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, 128);
+  const int64_t r_beg = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r_end = min(rows, r_beg + rows_per_chunk);
+  const int nst = r_end > r_beg ? (int)((r_end - r_beg + kGK - 1) / kGK) : 0;
+  const uint32_t raw_s = smem_u32(raw), core_s = smem_u32(core);
+  auto issue = [&](int st) {  // thread 0: stage st into raw buffer st % kBR
+    const int64_t r0 = r_beg + (int64_t)st * kGK;
+    const int nr = (int)min((int64_t)kGK, r_end - r0);
+    const uint32_t bytes = (uint32_t)nr * (uint32_t)ldx * 4u;
+    uint64_t* mb = &full[st % kBR];
+    mbar_expect_tx(mb, bytes);
+    bulk_g2s(raw_s + (uint32_t)((st % kBR) * G::Raw) * 4u, X + r0 * ldx, bytes, mb);
+  };
+  if (tid == 0)
+    for (int st = 0; st < kBR - 1 && st < nst; ++st) issue(st);
+  // stage s is use s / kBR of raw buffer s % kBR and commit s / 2 of MMA
+  // buffer s % 2, so the parities of their mbarrier phases are known
+  int st_fail = nst;
+  const int m = tid;  // this thread's column
+  for (int st = 0; st < nst; ++st) {
+    const int rb = st % kBR, cb = st & 1;
+    const bool w1 = mbar_wait(&full[rb], (uint32_t)((st / kBR) & 1));  // the raw stage landed
+    // the MMAs of stage st - 2, which read this MMA buffer, are done
+    const bool w2 = st < 2 || mbar_wait(&mmad[cb], (uint32_t)(((st - 2) >> 1) & 1));
+    if (!__syncthreads_and(w1 && w2)) { st_fail = st; break; }
+    const int nr = (int)min((int64_t)kGK, r_end - (r_beg + (int64_t)st * kGK));
+    const float* rs = raw + rb * G::Raw;
+    float* hi = core + cb * G::Core;
+    float* lo = hi + kGTile;
+#pragma unroll
+    for (int k = 0; k < kGK; k += 4) {
+      float4 x;
+      x.x = (k + 0 < nr && m < n) ? rs[(k + 0) * ldx + m] : 0.f;
+      x.y = (k + 1 < nr && m < n) ? rs[(k + 1) * ldx + m] : 0.f;
+      x.z = (k + 2 < nr && m < n) ? rs[(k + 2) * ldx + m] : 0.f;
+      x.w = (k + 3 < nr && m < n) ? rs[(k + 3) * ldx + m] : 0.f;
+      const int o = core_off(m, k, kGK);
+      if (SPLIT) {
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        *reinterpret_cast<float4*>(hi + o) = h;
+        *reinterpret_cast<float4*>(lo + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      } else {
+        *reinterpret_cast<float4*>(hi + o) = x;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::);
+    __syncthreads();  // raw buffer rb is free, the MMA buffer is written
+    if (tid == 0) {
+      if (st + kBR - 1 < nst) issue(st + kBR - 1);  // into the buffer of stage st - 1
+      asm volatile("tcgen05.fence::after_thread_sync;" ::);
+      const uint32_t base = core_s + (uint32_t)(cb * G::Core) * 4u;
+      const uint32_t lbase = base + (uint32_t)kGTile * 4u;
+#pragma unroll
+      for (int kk = 0; kk < kGK / 8; ++kk) {
+        const uint64_t da = smem_desc(base + kk * 256, 128, kGK * 32);
+        mma_tf32(tmem, da, da, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          const uint64_t dl = smem_desc(lbase + kk * 256, 128, kGK * 32);
+          mma_tf32(tmem, da, dl, idesc, 1u);
+          mma_tf32(tmem, dl, da, idesc, 1u);
+        }
+      }
+      mma_commit(&mmad[cb]);
+    }
+  }
+  bool ok = st_fail == nst;
+  if (ok) {
+    bool all = true;  // the last commit of each MMA buffer
+    for (int s2 = max(0, nst - 2); s2 < nst; ++s2)
+      all = mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1)) && all;
+    ok = __syncthreads_and(all);
+  } else {
+    if (tid == 0) atomicOr(&flags[2], 1);
+    // bounded waits: the MMAs committed and the bulk copies issued finish
+    // before the shared memory and tensor memory are released
+    for (int s2 = max(0, st_fail - 2); s2 < st_fail; ++s2)
+      mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1));
+    for (int s2 = st_fail; s2 < min(nst, st_fail + kBR - 1); ++s2)
+      mbar_wait(&full[s2 % kBR], (uint32_t)((s2 / kBR) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::);
+  __syncthreads();
+  float* out = partial + (int64_t)blockIdx.x * (128 * 128);
+  const int row = warp * 32 + lane;
+  const bool have = ok && nst > 0;
+  for (int c0 = 0; c0 < n; c0 += 16) {
+    float v[16];
+    if (have) {
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    }
+    if (row < n) {
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(&out[row * 128 + c0 + j]) =
+            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 128);
+}
+
 // ----------------------------------------------------------- cross Gram
 // For two blocks X1 (rows x n1) and X2 (rows x n2) whose columns are known to
 // be mutually orthogonal within each block (the rows of a sketch B, and of
@@ -802,14 +963,27 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
                                   GramRing<false>::Smem));
     SFD_CUDA(cudaFuncSetAttribute(k_tc_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   GramRing<true>::Smem));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram_bulk<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  GramBulk<false>::Smem));
+    SFD_CUDA(cudaFuncSetAttribute(k_tc_gram_bulk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  GramBulk<true>::Smem));
     attr.fetch_or(1u << dev);
   }
   int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kGK - 1) / kGK, kGramChunks));
   int64_t rpc = (rows + nchunks - 1) / nchunks;
   rpc = ((rpc + kGK - 1) / kGK) * kGK;
   nchunks = (int)std::max<int64_t>(1, (rows + rpc - 1) / rpc);
+  // rows on 16-byte boundaries and at most 128 floats long: one bulk copy per stage
+  const bool bulk = (ldx & 3) == 0 && ldx <= 128 && ((uintptr_t)X & 15) == 0;
   if (rows > 0) {
-    if (split)
+    if (bulk && split)
+      k_tc_gram_bulk<true><<<nchunks, kTcThreads, GramBulk<true>::Smem, s>>>(
+          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+    else if (bulk)
+      k_tc_gram_bulk<false><<<nchunks, kTcThreads, GramBulk<false>::Smem, s>>>(
+          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+    else if (split)
       k_tc_gram<true><<<nchunks, kTcThreads, GramRing<true>::Smem, s>>>(
           X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
     else

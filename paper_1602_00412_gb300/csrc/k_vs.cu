@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(256)
 // adds the parts up and updates the log-sum and the inverse norm of v
 // (norm_finalize_block, mode 1), so the step needs no separate reduction
 // launch.
+// WIDE: l > 128 (a row of B'^T takes two float4 per lane); otherwise one,
+// which leaves the registers to hold the next four rows while the current
+// four are reduced (the loads of iteration i + 1 are in flight during the
+// shuffles of iteration i).
+template <bool WIDE>
 __global__ void __launch_bounds__(256, 3)
     k_v_update(float* __restrict__ v, const float* __restrict__ Bt, int ld, int ell, int64_t d,
                const float* __restrict__ w, float* __restrict__ part, float* __restrict__ wpart,
@@ -178,22 +183,32 @@ __global__ void __launch_bounds__(256, 3)
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const float4* B4 = reinterpret_cast<const float4*>(Bt);
   const int ld4 = ld >> 2;
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const float4 q0 = lane < nvec ? ws[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 q1 = lane + 32 < nvec ? ws[lane + 32] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t stride = (int64_t)gridDim.x * 8 * 4;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 q0 = lane < nvec ? ws[lane] : z4;
+  const float4 q1 = WIDE && lane + 32 < nvec ? ws[lane + 32] : z4;
   float acc2 = 0.f;
   float4 wa0 = z4, wa1 = z4;  // next step's B' v partials, columns lane and lane + 32
-  for (int64_t j = ((int64_t)blockIdx.x * 8 + wp) * 4; j < d; j += nwarps * 4) {
-    float4 b0[4], b1[4];
-    float vv[4];
+  int64_t j = ((int64_t)blockIdx.x * 8 + wp) * 4;
+  float4 b0[4], b1[4];
+  float vv[4];
+  auto load = [&](int64_t jj, float4 (&c0)[4], float4 (&c1)[4], float (&cv)[4]) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const bool row = j + r < d;
-      b0[r] = row && lane < nvec ? B4[(j + r) * ld4 + lane] : z4;
-      b1[r] = row && lane + 32 < nvec ? B4[(j + r) * ld4 + lane + 32] : z4;
-      vv[r] = row && lane == 0 ? v[j + r] : 0.f;
+      const bool row = jj + r < d;
+      c0[r] = row && lane < nvec ? B4[(jj + r) * ld4 + lane] : z4;
+      c1[r] = WIDE && row && lane + 32 < nvec ? B4[(jj + r) * ld4 + lane + 32] : z4;
+      cv[r] = row && lane == 0 ? v[jj + r] : 0.f;
     }
+  };
+  // prefetch only where the registers allow it (one float4 per lane and row)
+  constexpr bool kPrefetch = !WIDE;
+  if (kPrefetch && j < d) load(j, b0, b1, vv);
+  for (; j < d; j += stride) {
+    float4 n0[4], n1[4];
+    float nvv[4];
+    if (!kPrefetch) load(j, b0, b1, vv);
+    else if (j + stride < d) load(j + stride, n0, n1, nvv);
     float s[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -201,10 +216,12 @@ __global__ void __launch_bounds__(256, 3)
       t = fmaf(b0[r].y, q0.y, t);
       t = fmaf(b0[r].z, q0.z, t);
       t = fmaf(b0[r].w, q0.w, t);
-      t = fmaf(b1[r].x, q1.x, t);
-      t = fmaf(b1[r].y, q1.y, t);
-      t = fmaf(b1[r].z, q1.z, t);
-      t = fmaf(b1[r].w, q1.w, t);
+      if (WIDE) {
+        t = fmaf(b1[r].x, q1.x, t);
+        t = fmaf(b1[r].y, q1.y, t);
+        t = fmaf(b1[r].z, q1.z, t);
+        t = fmaf(b1[r].w, q1.w, t);
+      }
       s[r] = warp_sum(t);
     }
     float nv[4];  // the new v (lane 0; 0 past d)
@@ -223,8 +240,18 @@ __global__ void __launch_bounds__(256, 3)
       const float y = __shfl_sync(0xffffffffu, nv[r], 0);
       wa0.x = fmaf(b0[r].x, y, wa0.x); wa0.y = fmaf(b0[r].y, y, wa0.y);
       wa0.z = fmaf(b0[r].z, y, wa0.z); wa0.w = fmaf(b0[r].w, y, wa0.w);
-      wa1.x = fmaf(b1[r].x, y, wa1.x); wa1.y = fmaf(b1[r].y, y, wa1.y);
-      wa1.z = fmaf(b1[r].z, y, wa1.z); wa1.w = fmaf(b1[r].w, y, wa1.w);
+      if (WIDE) {
+        wa1.x = fmaf(b1[r].x, y, wa1.x); wa1.y = fmaf(b1[r].y, y, wa1.y);
+        wa1.z = fmaf(b1[r].z, y, wa1.z); wa1.w = fmaf(b1[r].w, y, wa1.w);
+      }
+    }
+    if (kPrefetch && j + stride < d) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        b0[r] = n0[r];
+        if (WIDE) b1[r] = n1[r];
+        vv[r] = nvv[r];
+      }
     }
   }
   red4[wp][lane] = wa0;
@@ -306,8 +333,12 @@ void vs_step(const VsArgs& a, Workspace& ws, float* x, float* u, float* v, float
   k_btx_reduce<<<a.ell, 256, 0, s>>>(ws.wpart, kVsBlocks, a.ell, scal, w);
   SFD_LAUNCH_CHECK();
   spmv(*a.csc, u, v, ws.partial_rows, s);
-  k_v_update<<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, ws.wpart, a.scale_dev,
-                                       scal, counter);
+  if (a.ell > 128)
+    k_v_update<true><<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, ws.wpart,
+                                               a.scale_dev, scal, counter);
+  else
+    k_v_update<false><<<kVsBlocks, 256, 0, s>>>(v, a.Bt, a.ld, a.ell, a.d, w, part, ws.wpart,
+                                                a.scale_dev, scal, counter);
   SFD_LAUNCH_CHECK();
 }
 
