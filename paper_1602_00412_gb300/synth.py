@@ -110,12 +110,17 @@ def _chunks(n, size):
         yield a, min(n, a + size)
 
 
-def planted(n, d, mu, s, rank, scale, decay, noise, seed, cap=None, chunk=20000, name="planted"):
-    """Poisson(mu) Zipf(s) rows with a planted rank-`rank` signal (see module doc)."""
+def planted(n, d, mu, s, rank, scale, decay, noise, seed, cap=None, chunk=20000, name="planted",
+            row_seed=None):
+    """Poisson(mu) Zipf(s) rows with a planted rank-`rank` signal (see module doc).
+    row_seed (optional): the column factors y_j come from `seed` and the rows
+    from `row_seed`, so row blocks of one stream can be drawn independently."""
     rng = np.random.default_rng(seed)
     cdf = _zipf_cdf(d, s)
     sig = scale * decay ** np.arange(rank, dtype=np.float64)
     Y = rng.standard_normal((d, rank))
+    if row_seed is not None:
+        rng = np.random.default_rng(row_seed)
     counts = rng.poisson(mu, size=n)
     if cap is not None:
         counts = np.minimum(counts, cap)
@@ -231,6 +236,47 @@ def c3(seed=0, n=5_000_000):
 def c5(seed=0, n=2_000_000):
     """n=2,000,000, d=1,000,000, l=256: Poisson(80), Zipf(1.1), rank-64 planted 10*0.9^t, noise 0.05."""
     return planted(n, 1000000, 80, 1.1, 64, 10.0, 0.9, 0.05, seed, name="c5")
+
+
+def c3_chunk(seed, i, n=625_000):
+    """Chunk i of the chunk-parallel C3 stream (8 chunks of 625,000 rows make
+    the 5,000,000-row stream): the C3 row distribution drawn from seed (seed, 3, i)."""
+    return bow(n, 200000, 4.2, 0.8, 1.05, 2.0, [seed, 3, i], name="c3")
+
+
+def c5_chunk(seed, i, n=500_000):
+    """Chunk i of the C5 stream (4 chunks of 500,000 rows make its 2,000,000
+    rows): planted column factors from `seed`, rows from (seed, 5, i)."""
+    return planted(n, 1000000, 80, 1.1, 64, 10.0, 0.9, 0.05, seed, name="c5",
+                   row_seed=[seed, 5, i])
+
+
+def _call(args):
+    fn, a = args
+    return fn(*a)
+
+
+def parallel(fn, arg_list, processes=None):
+    """[fn(*a) for a in arg_list] in spawned worker processes (generation only)."""
+    import multiprocessing as mp
+    import os
+    procs = processes or min(len(arg_list), os.cpu_count() or 1)
+    if procs <= 1:
+        return [fn(*a) for a in arg_list]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_call, [(fn, a) for a in arg_list])
+
+
+def concat(parts, name=None):
+    """Rows of several CSR blocks (same d) one after another."""
+    ip = [np.asarray(parts[0].indptr, dtype=np.int64)]
+    off = ip[0][-1]
+    for p in parts[1:]:
+        q = np.asarray(p.indptr, dtype=np.int64)
+        ip.append(q[1:] - q[0] + off)
+        off = ip[-1][-1]
+    return CSR(np.concatenate(ip), np.concatenate([p.indices for p in parts]),
+               np.concatenate([p.values for p in parts]), parts[0].d, name or parts[0].name)
 
 
 WORKLOADS = {
