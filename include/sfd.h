@@ -234,7 +234,9 @@ int sfd_csr_spmm_ex(int64_t m, int64_t d, const int32_t* rowptr, const int32_t* 
                     float* Y, int32_t ldy, int32_t transpose, int32_t variant);
 
 /* Orthonormalise the columns of X (rows x k, leading dimension ld, device) in
- * place by CholeskyQR2 (the GramSchmidt step of Alg. 1), k <= 256. */
+ * place (the GramSchmidt step of Alg. 1), k <= 256, by shifted CholeskyQR3:
+ * three passes of Gram (FP32, fixed summation order), Cholesky factor of the
+ * shifted Gram and its inverse (FP64), X R^-1 (FP32). */
 int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld);
 
 /* ------------------------------------------------------------ many streams

@@ -178,11 +178,14 @@ void Slot::build(int m, int64_t nnz) {
 
 bool Slot::orth_pass(const float* X, int64_t rows, float* Xout, int form, __half* Xh) {
   const ColMap map = single_map(ell);
+  // the accurate passes of mixed precision (form 2) factor their Gram in FP64,
+  // also where l is too wide for the tensor-core Gram
+  const bool fp64 = form == 2;
   if (!tc_supported(ell, ell)) form = 0;
   const bool split = form == 2;
   if (form) gram_tc(X, ld, map, rows, ws.small_a, ws, stream, split);
   else gram(X, ld, map, rows, ws.small_a, ws, stream);
-  chol_inv(ws.small_a, ell, ws.small_b, ws.eig_work, ws.flags, stream);
+  chol_inv(ws.small_a, ell, ws.small_b, ws.eig_work, ws.flags, stream, fp64);
   if (form == 1) gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, Xh);
   else if (split && tc_split_supported(ell, ell))
     gemm_ts_tc(X, ld, map, rows, ws.small_b, ell, Xout, ld, ws, stream, nullptr, true);

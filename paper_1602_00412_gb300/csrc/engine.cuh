@@ -120,9 +120,10 @@ struct Slot {
  private:
   void cleanup();
   // CholeskyQR step X -> Xout. form 0: CUDA cores, FP32; 1: tensor cores,
-  // TF32 inputs; 2: tensor cores, split TF32 (FP32-accurate). Forms 1 and 2
-  // need l <= 128 (else form 0 runs). With form 1 and Xh, the result goes to
-  // Xh as fp16 only (returns true then).
+  // TF32 inputs; 2: tensor cores, split TF32 (FP32-accurate) and the l x l
+  // Cholesky in FP64. The tensor-core Grams need l <= 128 (else the CUDA-core
+  // Gram runs; form 2 keeps its FP64 Cholesky). With form 1 and Xh, the result
+  // goes to Xh as fp16 only (returns true then).
   bool orth_pass(const float* X, int64_t rows, float* Xout, int form, __half* Xh = nullptr);
   void spmm_timed(const Csr& c, const float* X, float* Yo, int64_t rows_in,
                   const __half* Xh = nullptr);

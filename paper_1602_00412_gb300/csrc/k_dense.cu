@@ -260,39 +260,68 @@ __device__ float block_sum_f(float v, float* red) {
 //    triangle. Rinv[r][c] = B[r][c] / R[r][r].
 constexpr int kCholThreads = 256;
 
+__device__ __forceinline__ float c_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double c_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float c_ldexp(float x, int e) { return ldexpf(x, e); }
+__device__ __forceinline__ double c_ldexp(double x, int e) { return ldexp(x, e); }
+
+__device__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+__device__ __forceinline__ float block_sum_t(float v, float* red) { return block_sum_f(v, red); }
+__device__ __forceinline__ double block_sum_t(double v, double* red) { return block_sum_d(v, red); }
+
+// T: the arithmetic type (float; double for the FP64 factorisation of the
+// accurate CholeskyQR passes). G is read and Rinv written as fp32 either way.
+template <typename T>
 __global__ void __launch_bounds__(kCholThreads)
     k_chol_inv(const float* __restrict__ G, int k, float* __restrict__ Rinv,
-               float* __restrict__ gA, int* __restrict__ flags, int use_smem) {
-  extern __shared__ float sh[];
-  __shared__ float red[33];
-  __shared__ float rdiag[kMaxEll];
+               T* __restrict__ gA, int* __restrict__ flags, int use_smem) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
+  __shared__ T red[33];
+  __shared__ T rdiag[kMaxEll];
   const int lda = k | 1;
-  float* A = use_smem ? sh : gA;
+  T* A = use_smem ? sh : gA;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  float tr = 0.f;
+  T tr = 0;
   for (int e = tid; e < k * k; e += nt) {
     int i = e / k, j = e % k;
-    float v = G[e];
+    T v = (T)G[e];
     A[i * lda + j] = v;
     if (i == j) tr += v;
   }
-  tr = block_sum_f(tr, red);
-  const float shift = tr > 0.f ? ldexpf(tr / (float)k, -20) : 1e-30f;
+  tr = block_sum_t(tr, red);
+  const T shift = tr > (T)0 ? c_ldexp(tr / (T)k, -20) : (T)1e-30f;
   for (int i = tid; i < k; i += nt) A[i * lda + i] += shift;
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    float p = A[j * lda + j];
-    if (!(p > 0.f)) p = shift;
-    const float ljj = sqrtf(p);
-    const float inv = 1.f / ljj;
+    T p = A[j * lda + j];
+    if (!(p > (T)0)) p = shift;
+    const T ljj = c_sqrt(p);
+    const T inv = (T)1 / ljj;
     if (tid == 0) {
       rdiag[j] = ljj;
-      if (!(A[j * lda + j] > 0.f)) atomicAdd(&flags[1], 1);
+      if (!(A[j * lda + j] > (T)0)) atomicAdd(&flags[1], 1);
     }
     for (int t = j + 1 + tid; t < k; t += nt) A[j * lda + t] = A[t * lda + j] * inv;
     for (int i = j + 1 + warp; i < k; i += nw) {
-      const float lij = A[i * lda + j] * inv;
+      const T lij = A[i * lda + j] * inv;
       for (int t = j + 1 + lane; t <= i; t += 32) A[i * lda + t] -= lij * (A[t * lda + j] * inv);
     }
     __syncthreads();
@@ -300,21 +329,21 @@ __global__ void __launch_bounds__(kCholThreads)
   // B = I in the lower triangle (B[i][c] at A[c][i], i <= c)
   for (int e = tid; e < k * k; e += nt) {
     int c = e / k, i = e % k;
-    if (i <= c) A[c * lda + i] = i == c ? 1.f : 0.f;
+    if (i <= c) A[c * lda + i] = i == c ? (T)1 : (T)0;
   }
   __syncthreads();
   for (int j = k - 1; j > 0; --j) {
-    const float rj = 1.f / rdiag[j];
+    const T rj = (T)1 / rdiag[j];
     // B[i][c] -= R[i][j] * B[j][c] / R[j][j]   for i < j <= c
     for (int c = j + warp; c < k; c += nw) {
-      const float xjc = A[c * lda + j] * rj;
+      const T xjc = A[c * lda + j] * rj;
       for (int i = lane; i < j; i += 32) A[c * lda + i] -= A[i * lda + j] * xjc;
     }
     __syncthreads();
   }
   for (int e = tid; e < k * k; e += nt) {
     int r = e / k, c = e % k;
-    Rinv[e] = c >= r ? A[c * lda + r] / rdiag[r] : 0.f;
+    Rinv[e] = c >= r ? (float)(A[c * lda + r] / rdiag[r]) : 0.f;
   }
 }
 
@@ -418,23 +447,33 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
   SFD_LAUNCH_CHECK();
 }
 
-void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s) {
-  if (k <= 128) {
+void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s,
+              bool fp64) {
+  if (!fp64 && k <= 128) {
     chol_inv_blk(G, k, Rinv, flags, s);
     return;
   }
   const int lda = k | 1;
-  size_t bytes = (size_t)k * lda * sizeof(float);
-  int use_smem = bytes <= 200 * 1024;
+  const size_t bytes = (size_t)k * lda * (fp64 ? sizeof(double) : sizeof(float));
+  const int use_smem = bytes <= 200 * 1024;
   static std::atomic<unsigned> attr_set{0};  // one bit per device
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
   if (dev < 32 && !(attr_set.load() & (1u << dev))) {
-    SFD_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SFD_CUDA(cudaFuncSetAttribute(k_chol_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    SFD_CUDA(cudaFuncSetAttribute(k_chol_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
     attr_set.fetch_or(1u << dev);
   }
-  k_chol_inv<<<1, kCholThreads, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags, use_smem);
+  // work: k * lda scalars when the matrix does not fit in shared memory (the
+  // eigensolver scratch, 256-byte aligned, is far larger)
+  if (fp64)
+    k_chol_inv<double><<<1, kCholThreads, use_smem ? bytes : 0, s>>>(
+        G, k, Rinv, reinterpret_cast<double*>(work), flags, use_smem);
+  else
+    k_chol_inv<float><<<1, kCholThreads, use_smem ? bytes : 0, s>>>(G, k, Rinv, work, flags,
+                                                                    use_smem);
   SFD_LAUNCH_CHECK();
 }
 

@@ -239,9 +239,12 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
     alloc_dense_scratch(A, ws);
     float* tmp = A.alloc<float>((size_t)rows * ld);
     const ColMap map = single_map(k);
-    for (int pass = 0; pass < 2; ++pass) {  // CholeskyQR2
+    // shifted CholeskyQR3: the first (shifted) pass leaves a block of condition
+    // number about sqrt(||X||^2 / shift) <= 2^10 whatever cond(X) was; the
+    // next two make it orthonormal to fp32 accuracy
+    for (int pass = 0; pass < 3; ++pass) {
       gram(X, ld, map, rows, ws.small_a, ws, s);
-      chol_inv(ws.small_a, k, ws.small_b, ws.eig_work, ws.flags, s);
+      chol_inv(ws.small_a, k, ws.small_b, ws.eig_work, ws.flags, s, true);  // FP64 factor
       gemm_ts(X, ld, map, rows, ws.small_b, k, tmp, ld, s);
       SFD_CUDA(cudaMemcpy2DAsync(X, ld * sizeof(float), tmp, ld * sizeof(float), k * sizeof(float),
                                  rows, cudaMemcpyDeviceToDevice, s));

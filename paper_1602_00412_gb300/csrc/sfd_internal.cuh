@@ -196,8 +196,10 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
                 bool split = false);
 // Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
 // row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
-// clamped.
-void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s);
+// clamped. fp64: factorisation and inverse in double (one CTA; work holds
+// k (k|1) doubles when they do not fit in shared memory), else fp32.
+void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s,
+              bool fp64 = false);
 // The blocked one-CTA form used by chol_inv for k <= 128.
 void chol_inv_blk(const float* G, int k, float* Rinv, int* flags, cudaStream_t s);
 // Largest nwant eigenpairs of the symmetric n x n S: evals (descending),

@@ -121,7 +121,8 @@ def test_spmm_is_deterministic(lib):
 @pytest.mark.parametrize("rows,k,cond", [(5000, 50, 10.0), (50000, 100, 1e3), (3000, 200, 1e2),
                                          (700, 256, 10.0), (64, 8, 1.0), (1000, 1, 1.0),
                                          (999, 17, 10.0), (2000, 127, 1e2), (4000, 128, 1e3),
-                                         (500, 16, 1e3), (800, 33, 1e2)])
+                                         (500, 16, 1e3), (800, 33, 1e2), (20000, 64, 1e4),
+                                         (20000, 100, 1e5), (10000, 50, 1e6)])
 def test_orthonormalize(lib, rows, k, cond):
     rng = np.random.default_rng(rows + k)
     U, _ = np.linalg.qr(rng.standard_normal((rows, k)))
