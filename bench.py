@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
     ap.add_argument("--no-forms", action="store_true",
-                    help="time only the chosen form (not the plain FP32 and verify-off forms)")
+                    help="time only the chosen form (not the plain FP32, verify-off and "
+                         "learned-q forms)")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="0: FP32 throughout; 1: tensor-core (TF32) Gram and X R^-1 in the "
                          "orthonormalisations of all but the last power iteration")
@@ -61,7 +62,7 @@ def parse():
     ap.add_argument("--train-rows", type=int, default=400_000,
                     help="rows of each labelled training stream (learned q)")
     ap.add_argument("--train-streams", type=int, default=2)
-    ap.add_argument("--q-margin", type=float, default=2.0,
+    ap.add_argument("--q-margin", type=float, default=3.0,
                     help="learned q: q = ceil(prediction + margin), clamped to the schedule")
     return ap.parse_args()
 
@@ -405,7 +406,7 @@ def ours_arm(args, rank, world, local):
           "vv_h": torch.from_numpy(X.values).pin_memory().numpy(),
           "B_h": torch.empty((ell, d), dtype=torch.float32).pin_memory().numpy()}
     theta, qinfo = (None, None)
-    if args.q_mode == "learned":
+    if args.q_mode == "learned" or not args.no_forms:
         theta, qinfo = train_q_model(sfd, args, d, ell)
     learned = args.q_mode == "learned"
     chosen = Form("chosen", precision=args.precision, q_mode=1 if learned else 0, profile=1)
@@ -420,6 +421,9 @@ def ours_arm(args, rank, world, local):
         forms.append(time_form(Form("verify_off", precision=args.precision, verify=0,
                                     q_mode=1 if learned else 0), sfd, io, args, world, stream,
                                theta, e2e=False))
+        if not learned:  # the learned power count (network trained above)
+            forms.append(time_form(Form("learned", precision=args.precision, q_mode=1), sfd, io,
+                                   args, world, stream, theta, e2e=False))
     nnz_all = int(over_ranks(X.nnz, world, "sum"))   # each rank's stream has its own seed
     rate = lambda ms: whole_job_rate(nnz_all, args.steps, ms) if ms else None
     st = chosen.stats
@@ -447,8 +451,7 @@ def ours_arm(args, rank, world, local):
            "dtype": "f32" if args.precision == 0 else "tf32+f32", "data": "synthetic",
            "config": {"workload": DESC, "rows": X.n, "d": d, "ell": ell, "nnz_per_rank": X.nnz,
                       "precision": ["fp32", "mixed-tf32"][args.precision],
-                      "q_mode": args.q_mode, "q_model": qinfo,
-                      "q_margin": args.q_margin if learned else None,
+                      "q_mode": args.q_mode, "q_model": qinfo, "q_margin": args.q_margin,
                       "buffers_per_step": st["buffers"], "attempts_per_step": st["attempts"],
                       "q_per_attempt": st["q_total"] / max(1, st["attempts"]),
                       "l2": "inputs larger than L2 (CSR stream %.0f MB per rank)" % (

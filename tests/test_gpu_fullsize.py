@@ -134,3 +134,34 @@ def test_largest_l_stream_matches_oracle(lib):
     ce, ce_ref = metrics.cov_err(A, B), metrics.cov_err(A, ref)
     assert abs(ce - ce_ref) <= 0.02 * ce_ref
     assert metrics.cov_norm(A, B) <= metrics.fd_bound(A, ell, 64)
+
+
+def test_c2_learned_power_count_matches_oracle(lib, c2):
+    # the learned form on the whole C2 stream with its trained network (labels
+    # logged on two 400,000-row streams of other seeds, as bench.py does):
+    # fewer power iterations, cov-err within 2 % of the FP64 oracle's
+    d, ell = 50000, 100
+    feats, labels = [], []
+    for s in range(2):
+        Xt = synth.c2(seed=1000 + s, n=400_000)
+        t = lib.SFD(d, ell, 1000 + s, q_mode=2, precision=1)
+        t.append(Xt.indptr, Xt.indices, Xt.values)
+        t.sketch()
+        F, L, _ = t.q_log()
+        t.close()
+        feats.append(F)
+        labels.append(L)
+    theta, _ = lib.sfd_q_train(np.concatenate(feats), np.concatenate(labels),
+                               lib.q_init_params(0), epochs=300, batch=8, lr=3e-3)
+    s = lib.SFD(d, ell, 0, precision=1, q_mode=1, q_margin=3.0)
+    s.set_q_model(theta)
+    s.append(c2.indptr, c2.indices, c2.values)
+    B = s.sketch()
+    st = s.stats()
+    s.close()
+    assert st["buffers"] == 20 and st["unverified"] == 0
+    assert st["q_total"] / st["attempts"] < 13
+    A = c2.to_scipy()
+    g = _golden_c2()
+    ce = _residual_top(A, B) / metrics.fro2(A)
+    assert abs(ce - g["cov_err"]) <= 0.02 * g["cov_err"], (ce, g["cov_err"])
