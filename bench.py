@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--rows", type=int, default=WORKLOAD["n"], help="stream length (default: full)")
     ap.add_argument("--no-check", action="store_true", help="skip the cov-err evaluation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--experiment", default=None, choices=["paper-table1"],
+                    help="instead of the benchmark: the paper's Sec. 5 comparison of SFD and "
+                         "FrequentDirections on its synthetic data, over the ranges of Table 1")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
     ap.add_argument("--no-forms", action="store_true",
                     help="time only the chosen form (not the plain FP32, verify-off and "
@@ -500,13 +503,82 @@ def ours_arm(args, rank, world, local):
     if rank == 0:
         print(json.dumps(out), flush=True)
 
+# ------------------------------------------------------- paper, Table 1
+TABLE1_DEFAULT = {"n": 10000, "d": 1000, "ell": 50, "z": 100}
+TABLE1_RANGES = {"n": [10000, 20000, 40000, 60000], "d": [1000, 2000, 4000, 6000],
+                 "ell": [5, 10, 20, 50, 100], "z": [5, 10, 50, 100, 200, 500]}
+
+
+def proj_err_check(A, B, k, tail):
+    """proj-err = ||A - A V_k V_k^T||_F^2 / ||A - A_k||_F^2, V_k the top-k right
+    singular vectors of B (Sec. 5, Measurements)."""
+    import numpy as np
+    _, _, Vt = np.linalg.svd(B.astype(np.float64), full_matrices=False)
+    AV = A @ Vt[:k].T
+    fro2 = float(A.multiply(A).sum())
+    return (fro2 - float((np.asarray(AV) ** 2).sum())) / tail
+
+
+def paper_table1(args):
+    """The comparison of Sec. 5 on its synthetic data (+-1 entries, z per row,
+    head of 1.5 z columns drawn w.p. 0.9), one parameter of Table 1 varied at a
+    time: classical FrequentDirections (mode 1) against SFD with SparseShrink
+    called directly (verify 0, as the paper runs it), both on this GPU; k = 10.
+    Prints one JSON line per point."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+    import torch
+    from paper_1602_00412_gb300.build import build
+    build()
+    from paper_1602_00412_gb300 import sfd, synth
+    k = 10
+    for param, values in TABLE1_RANGES.items():
+        for v in values:
+            p = dict(TABLE1_DEFAULT, **{param: v})
+            n, d, ell, z = p["n"], p["d"], p["ell"], p["z"]
+            X = synth.headtail(n, d, z, 0)
+            A = X.to_scipy()
+            ip = torch.from_numpy(X.indptr).cuda()
+            ix = torch.from_numpy(X.indices.astype(np.int32)).cuda()
+            vv = torch.from_numpy(X.values.astype(np.float32)).cuda()
+            fro2 = float(A.multiply(A).sum())
+            kk = min(k, ell - 1)
+            sv = spla.svds(A, k=kk, tol=1e-8, return_singular_vectors=False)
+            tail = fro2 - float((sv ** 2).sum())
+            line = {"experiment": "paper Table 1", "param": param, "n": n, "d": d, "ell": ell,
+                    "nnz_per_row": z, "k": kk}
+            for name, opts in (("fd", {"mode": 1}), ("sfd", {"verify": 0})):
+                ctx = sfd.SFD(d, ell, 0, **opts)
+                B = torch.empty((ell, d), device="cuda")
+                times = []
+                for rep in range(4):      # one warm-up, then the median of three
+                    ctx.reset()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    ctx.append(ip, ix, vv)
+                    ctx.sketch(B)
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(time.perf_counter() - t0)
+                ctx.close()
+                Bh = B.cpu().numpy()
+                acc = cov_err_check(X, Bh, kk)
+                line[name] = {"seconds": statistics.median(times), "cov_err": acc["cov_err"],
+                              "proj_err": proj_err_check(A, Bh, kk, tail)}
+            line["fd_over_sfd_time"] = line["fd"]["seconds"] / line["sfd"]["seconds"]
+            print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    if args.impl == "reference":
+    if args.experiment == "paper-table1":
+        if rank == 0:
+            paper_table1(args)
+    elif args.impl == "reference":
         reference_arm(args, rank, world)
     else:
         ours_arm(args, rank, world, local)

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SFD_ABI_VERSION 3u
+#define SFD_ABI_VERSION 4u
 
 #define SFD_OK 0
 #define SFD_EINVAL 1   /* bad argument: l < 1, l > d, index outside [0,d), non-monotone indptr, NaN/Inf value, ... */
@@ -86,6 +86,9 @@ typedef struct sfd_options {
   int32_t autotune;     /* 1 (default): each slot times the unroll variants of its sparse
                            products on first use and keeps the fastest per pass (the variants
                            give identical results); 0: the default variant */
+  int32_t mode;         /* 0: Sparse Frequent Directions (Alg. 2, default); 1: the classical
+                           FrequentDirections of Sec. 3.1, for comparison (Sec. 5): every l rows
+                           B = DenseShrink([B; rows]) (Alg. 5), no SparseShrink */
 } sfd_options;
 
 /* Counters of a context (Alg. 2 / Alg. 4 bookkeeping). */
@@ -164,7 +167,7 @@ int sfd_merge(sfd_ctx* dst, sfd_ctx* src);
  * state is taken as it stands after the last call (every call leaves no
  * buffer in flight). The blob holds d, l, seed, b, the options that decide
  * the result (delta, verify, c_q, q_override, retry_cap, precision, q_mode,
- * strict, q_margin, q_tau), the counters, B (l x d float32), the open buffer
+ * strict, q_margin, q_tau, mode), the counters, B (l x d float32), the open buffer
  * (int32 row pointer, int32 columns, float32 values), the learned-q network
  * when one is set (not the q_mode 2 label log), and an FNV-1a hash; host
  * byte order. Errors: SFD_EINVAL (cap too small), SFD_ENOMEM, SFD_ECUDA. */

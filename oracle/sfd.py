@@ -11,6 +11,9 @@ Algorithm for Sparse Matrices", in the paper's order and notation:
   dense_shrink            Alg. 5
   verify_spectral         Alg. 6 (Sec. 4.1, Lemma 4.1)
   frequent_directions     the classical FD of Sec. 3.1 (baseline only)
+  frequent_directions_stream
+                          classical FD with a buffer of l rows, as the
+                          comparison mode of the GPU library runs it (Sec. 5)
 
 Readings of points the paper leaves open (the same on the CUDA side):
 
@@ -328,3 +331,17 @@ def frequent_directions(A, ell):
     out = np.zeros((ell, d))
     out[:B.shape[0]] = B
     return out
+
+
+def frequent_directions_stream(A, ell):
+    """Classical FD (Sec. 3.1) driven like Alg. 2 with a buffer of l rows:
+    B = 0 (l x d); after every l rows, and for the rows left at the end,
+    B = DenseShrink([B; rows], l) (Alg. 5). Every shrink subtracts the l-th
+    squared singular value of the stack in each kept direction, which is the
+    FD step, so the FD guarantee of Sec. 3.1 holds for the result."""
+    A = A.toarray() if sp.issparse(A) else np.asarray(A, dtype=np.float64)
+    n, d = A.shape
+    B = np.zeros((ell, d))
+    for i in range(0, n, ell):
+        B = dense_shrink(np.vstack([B, A[i:i + ell]]), ell)
+    return B

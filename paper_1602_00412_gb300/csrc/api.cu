@@ -182,7 +182,7 @@ int close_buffer(Ctx& C) {
   memcpy(S.ptr_host, C.h_ptr.data(), (m + 1) * sizeof(int));
   SFD_CUDA(cudaMemcpyAsync(S.csr.ptr, S.ptr_host, (m + 1) * sizeof(int), cudaMemcpyHostToDevice,
                            S.stream));
-  if (m >= C.ell) {
+  if (m >= C.ell && C.opt.mode == 0) {
     S.build(m, C.pend_nnz);
     const int q = q_for(C.opt, m);
     QControl qc;
@@ -199,7 +199,8 @@ int close_buffer(Ctx& C) {
                                          C.opt.verify, &qc);
     C.fifo.push_back({C.fill, C.b, m, q_used, 0, q});
   } else {
-    // too few rows for SparseShrink: DenseShrink([B; A']) with A' dense
+    // too few rows for SparseShrink, or classical FrequentDirections (mode 1):
+    // DenseShrink([B; A']) with A' dense
     status = drain(C);
     S.wait_freed();
     SFD_CUDA(cudaMemsetAsync(S.Bpt, 0, (size_t)C.d * S.ld * sizeof(float), S.stream));
@@ -276,6 +277,7 @@ int sfd_create(int64_t d, int32_t ell, uint64_t seed, const sfd_options* opt, sf
   if (opt) C.opt = *opt; else sfd_options_init(&C.opt);
   if (!(C.opt.delta > 0 && C.opt.delta < 1) || C.opt.c_q < 0 || C.opt.slots < 0 ||
       (C.opt.precision != 0 && C.opt.precision != 1) || C.opt.q_mode < 0 || C.opt.q_mode > 2 ||
+      (C.opt.mode != 0 && C.opt.mode != 1) ||
       !(C.opt.q_tau >= 0.f && C.opt.q_tau < 1.f) || !(C.opt.q_margin > -64.f && C.opt.q_margin < 64.f)) {
     delete ctx;
     return SFD_EINVAL;
@@ -387,7 +389,9 @@ int sfd_append_rows(sfd_ctx* ctx, int64_t nrows, const int64_t* indptr, const in
     }
     SFD_CUDA(cudaEventRecord(C.in_ready, C.in_stream));
     // 3. Alg. 2: one row at a time; close the buffer when nnz >= l d or rows = d
-    const int64_t thresh = (int64_t)C.ell * C.d;
+    //    (classical FrequentDirections, mode 1: every l rows)
+    const int64_t thresh = C.opt.mode == 1 ? INT64_MAX : (int64_t)C.ell * C.d;
+    const int64_t row_cap = C.opt.mode == 1 ? C.ell : C.d;
     int status = SFD_OK;
     auto keep = [&status](int rc) {
       if (rc != SFD_OK) status = rc;
@@ -414,7 +418,7 @@ int sfd_append_rows(sfd_ctx* ctx, int64_t nrows, const int64_t* indptr, const in
     for (int64_t i = 0; i < nrows; ++i) {
       rows_in_buf += 1;
       nnz_in_buf += ip[i + 1] - ip[i];
-      if (nnz_in_buf >= thresh || rows_in_buf == C.d) {
+      if (nnz_in_buf >= thresh || rows_in_buf == row_cap) {
         copy_rows(seg_start, i + 1);
         seg_start = i + 1;
         keep(close_buffer(C));

@@ -13,7 +13,7 @@
 //   char[8]  magic "SFDCKPT1"
 //   u32      SFD_ABI_VERSION, u32 header bytes (kHeaderBytes)
 //   i64 d, i32 l, i32 has_qmodel, u64 seed, i64 b,
-//   i64 pending rows, i64 pending entries, i32 inject_left, i32 0,
+//   i64 pending rows, i64 pending entries, i32 inject_left, i32 mode,
 //   options: f64 delta, i32 verify, f64 c_q, i32 q_override, i32 retry_cap,
 //            i32 precision, i32 q_mode, i32 strict, f32 q_margin, f32 q_tau
 //   stats: sfd_stats field by field (i64 / f64, 8 bytes each)
@@ -122,7 +122,7 @@ std::vector<unsigned char> serialize(Ctx& C) {
   w.put<int64_t>(C.pend_rows);
   w.put<int64_t>(C.pend_nnz);
   w.put<int32_t>(C.inject_left);
-  w.put<int32_t>(0);
+  w.put<int32_t>(C.opt.mode);
   const sfd_options& o = C.opt;
   w.put<double>(o.delta);
   w.put<int32_t>(o.verify);
@@ -212,9 +212,10 @@ int sfd_load(const void* buf, int64_t size, const sfd_options* runtime, sfd_ctx*
   const int64_t b = r.get<int64_t>();
   const int64_t prow = r.get<int64_t>(), pnnz = r.get<int64_t>();
   const int32_t inject = r.get<int32_t>();
-  r.get<int32_t>();
+  const int32_t mode = r.get<int32_t>();
   sfd_options o;
   sfd_options_init(&o);
+  o.mode = mode;
   o.delta = r.get<double>();
   o.verify = r.get<int32_t>();
   o.c_q = r.get<double>();

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libsfd.so")
 
-SFD_ABI_VERSION = 3
+SFD_ABI_VERSION = 4
 SFD_OK, SFD_EINVAL, SFD_ENOMEM, SFD_ECUDA, SFD_EVERIFY, SFD_ETIMEOUT = 0, 1, 2, 3, 4, 5
 SFD_HOST, SFD_DEVICE = 0, 1
 
@@ -31,7 +31,7 @@ class sfd_options(ctypes.Structure):
                 ("strict", ctypes.c_int32), ("inject_vs_fail", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("q_margin", ctypes.c_float), ("q_tau", ctypes.c_float),
-                ("autotune", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("mode", ctypes.c_int32)]
 
 
 class sfd_stats(ctypes.Structure):

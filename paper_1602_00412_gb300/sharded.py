@@ -27,8 +27,8 @@ import struct
 import numpy as np
 
 MAGIC = b"SFDCKPT1"
-ABI_VERSION = 3
-_HEAD = "<8sIIqiiQqqqii"          # magic .. inject_left, pad
+ABI_VERSION = 4
+_HEAD = "<8sIIqiiQqqqii"          # magic .. inject_left, mode
 _OPTS = "<didiiiiiff"             # delta verify c_q q_override retry_cap precision q_mode strict q_margin q_tau
 _STATS_I = ("rows_seen", "nnz_seen", "buffers", "attempts", "vs_rejects", "unverified",
             "q_total", "pending_rows", "pending_nnz")
@@ -57,13 +57,14 @@ def parse_checkpoint(blob, check_hash=True):
         raise ValueError("checkpoint hash mismatch")
     f = {}
     (magic, abi, hb, f["d"], f["ell"], has_q, f["seed"], f["b"], prow, pnnz, f["inject_left"],
-     _) = struct.unpack_from(_HEAD, blob, 0)
+     mode) = struct.unpack_from(_HEAD, blob, 0)
     if magic != MAGIC or abi != ABI_VERSION or hb != HEADER_BYTES:
         raise ValueError("not a checkpoint of this library version")
     at = struct.calcsize(_HEAD)
     o = struct.unpack_from(_OPTS, blob, at)
     f["options"] = dict(zip(("delta", "verify", "c_q", "q_override", "retry_cap", "precision",
                              "q_mode", "strict", "q_margin", "q_tau"), o))
+    f["options"]["mode"] = mode
     at += struct.calcsize(_OPTS)
     st = struct.unpack_from(_STATS, blob, at)
     f["stats"] = dict(zip(_STATS_I + _STATS_F + ("kernel_launches", "spmm_launches", "spmm_ms",
@@ -101,7 +102,7 @@ def pack_checkpoint(f):
     parts = [
         struct.pack(_HEAD, MAGIC, ABI_VERSION, HEADER_BYTES, d, ell, int(qp is not None),
                     int(f["seed"]), int(f["b"]), len(ptr) - 1, len(idx),
-                    int(f.get("inject_left", 0)), 0),
+                    int(f.get("inject_left", 0)), int(o.get("mode", 0))),
         struct.pack(_OPTS, o["delta"], o["verify"], o["c_q"], o["q_override"], o["retry_cap"],
                     o["precision"], o["q_mode"], o["strict"], o["q_margin"], o["q_tau"]),
         struct.pack(_STATS, *[int(st.get(k, 0)) for k in _STATS_I],

@@ -449,3 +449,25 @@ def test_cov_norm_operator_path_matches_dense():
     dense = metrics.cov_norm(A, B, dense_limit=4000)
     op = metrics.cov_norm(A, B, dense_limit=100)
     assert math.isclose(dense, op, rel_tol=1e-6)
+
+
+def test_fd_stream_exact_below_l_and_bound():
+    # fewer rows than l: the stack [0; A] has rank < l, its l-th singular value
+    # is 0, nothing is shrunk and B^T B = A^T A exactly
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((7, 30))
+    B = O.frequent_directions_stream(A, 10)
+    assert np.allclose(B.T @ B, A.T @ A, atol=1e-10)
+    # many rows: Prop. 1 and the FD bound for every k < l (Sec. 3.1)
+    X = synth.headtail(400, 120, 12, 3)
+    A = X.to_scipy()
+    for ell in (5, 12):
+        B = O.frequent_directions_stream(A, ell)
+        lo, hi = metrics.residual_eigs(A, B)
+        assert lo > -1e-9 * metrics.fro2(A)
+        for k in range(ell):
+            assert hi <= metrics.fd_bound(A, ell, k) * (1 + 1e-9)
+    # the last shrink of a stream of exactly l rows is DenseShrink([0; A])
+    A = rng.standard_normal((10, 40))
+    assert np.allclose(O.frequent_directions_stream(A, 10),
+                       O.dense_shrink(np.vstack([np.zeros((10, 40)), A]), 10))

@@ -28,7 +28,7 @@ from paper_1602_00412_gb300 import synth  # noqa: E402
 
 D, ELL, SEED, N = 300, 12, 7, 2400
 OPTS = {"delta": 0.01, "verify": 1, "c_q": 0.25, "q_override": -1, "retry_cap": 8,
-        "precision": 0, "q_mode": 0, "strict": 0, "q_margin": 1.0, "q_tau": 0.01}
+        "precision": 0, "q_mode": 0, "strict": 0, "q_margin": 1.0, "q_tau": 0.01, "mode": 0}
 
 
 def _stream():
