@@ -449,8 +449,8 @@ void gemm_ts(const float* X, int ldx, ColMap map, int64_t rows, const float* T, 
 
 void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s,
               bool fp64) {
-  if (!fp64 && k <= 128) {
-    chol_inv_blk(G, k, Rinv, flags, s);
+  if (chol_blk_supported(k, fp64)) {  // blocked one-CTA form: fp32 k <= 128, fp64 k <= 112
+    chol_inv_blk(G, k, Rinv, flags, s, fp64);
     return;
   }
   const int lda = k | 1;

@@ -482,25 +482,25 @@ __global__ void __launch_bounds__(256)
     const int2 it = items[item];
     seg = it.x;
     const int end = min(it.y + kSplit, ptr[seg + 1]);
-    // four entries per lane at a time: their column indices and values are
-    // loaded first, then the four gathers of x are in flight together; the
-    // products are added in the lane's entry order (the same sum as one
-    // entry at a time)
-    int p = it.y + gl;
-    for (; p + 24 < end; p += 32) {
+    // four entries per lane at a time, the last group predicated: their
+    // column indices and values are loaded first, then the four gathers of x
+    // are in flight together; the products are added in the lane's entry
+    // order (the same sum as one entry at a time)
+    for (int p = it.y + gl; p < end; p += 32) {
       int c[4];
       float v[4], xv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        c[u] = idx[p + 8 * u];
-        v[u] = val[p + 8 * u];
+        const bool in = p + 8 * u < end;
+        c[u] = in ? idx[p + 8 * u] : 0;
+        v[u] = in ? val[p + 8 * u] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = __ldg(&x[c[u]]);
+      for (int u = 0; u < 4; ++u) xv[u] = p + 8 * u < end ? __ldg(&x[c[u]]) : 0.f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a = fmaf(v[u], xv[u] * xs, a);
+      for (int u = 0; u < 4; ++u)
+        if (p + 8 * u < end) a = fmaf(v[u], xv[u] * xs, a);
     }
-    for (; p < end; p += 8) a = fmaf(val[p], __ldg(&x[idx[p]]) * xs, a);
   }
   a += __shfl_xor_sync(0xffffffffu, a, 4);
   a += __shfl_xor_sync(0xffffffffu, a, 2);

@@ -201,7 +201,10 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
 void chol_inv(const float* G, int k, float* Rinv, float* work, int* flags, cudaStream_t s,
               bool fp64 = false);
 // The blocked one-CTA form used by chol_inv for k <= 128.
-void chol_inv_blk(const float* G, int k, float* Rinv, int* flags, cudaStream_t s);
+void chol_inv_blk(const float* G, int k, float* Rinv, int* flags, cudaStream_t s,
+                  bool fp64 = false);
+// Whether the blocked form fits one CTA's shared memory (fp64: k <= 112).
+bool chol_blk_supported(int k, bool fp64);
 // Largest nwant eigenpairs of the symmetric n x n S: evals (descending),
 // evecs n x nwant row-major. psd: S is a Gram matrix (positive semi-definite),
 // which allows the one-sided Jacobi path for n <= 128; otherwise (or for
