@@ -482,23 +482,24 @@ __global__ void __launch_bounds__(256)
     const int2 it = items[item];
     seg = it.x;
     const int end = min(it.y + kSplit, ptr[seg + 1]);
-    // four entries per lane at a time, the last group predicated: their
-    // column indices and values are loaded first, then the four gathers of x
-    // are in flight together; the products are added in the lane's entry
-    // order (the same sum as one entry at a time)
-    for (int p = it.y + gl; p < end; p += 32) {
-      int c[4];
-      float v[4], xv[4];
+    // eight entries per lane at a time (an item of up to 64 entries, most rows
+    // of a buffer, in one round), the last group predicated: their column
+    // indices and values are loaded first, then the eight gathers of x are in
+    // flight together; the products are added in the lane's entry order (the
+    // same sum as one entry at a time)
+    for (int p = it.y + gl; p < end; p += 64) {
+      int c[8];
+      float v[8], xv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const bool in = p + 8 * u < end;
         c[u] = in ? idx[p + 8 * u] : 0;
         v[u] = in ? val[p + 8 * u] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = p + 8 * u < end ? __ldg(&x[c[u]]) : 0.f;
+      for (int u = 0; u < 8; ++u) xv[u] = p + 8 * u < end ? __ldg(&x[c[u]]) : 0.f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 8; ++u)
         if (p + 8 * u < end) a = fmaf(v[u], xv[u] * xs, a);
     }
   }
