@@ -159,8 +159,20 @@ __global__ void __launch_bounds__(32 * kRedGroups)
     const int off = (a % kT) * kT + (c % kT);
     const float* p = partial + (int64_t)tp * (kT * kT) + off;
     const int64_t stride = (int64_t)npairs * (kT * kT);
+    // chunks grp, grp + 16, ... into s0 and grp + 8, grp + 24, ... into s1,
+    // in that order; eight loads are issued before their adds
     float s0 = 0.f, s1 = 0.f;
     int ch = grp;
+    for (; ch + 7 * kRedGroups < nchunks; ch += 8 * kRedGroups) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(p + (int64_t)(ch + u * kRedGroups) * stride);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        s0 += v[u];
+        s1 += v[u + 1];
+      }
+    }
     for (; ch + kRedGroups < nchunks; ch += 2 * kRedGroups) {
       s0 += p[ch * stride];
       s1 += p[(ch + kRedGroups) * stride];

@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kTcThreads)
 // read them have completed), so the per-element copies of k_tc_gram become
 // one instruction per stage plus shared-memory moves.
 constexpr int kBR = 6;  // raw stages in flight
+constexpr int kGramThreads = 256;
 template <bool SPLIT>
 struct GramBulk {
   static constexpr int Raw = kGK * 128;                          // floats per raw stage (ldx <= 128)
@@ -308,7 +309,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kGramThreads)
     k_tc_gram_bulk(const float* __restrict__ X, int ldx, int n, int64_t rows,
                    int64_t rows_per_chunk, float* __restrict__ partial, int* __restrict__ flags) {
   using G = GramBulk<SPLIT>;
@@ -349,7 +350,8 @@ __global__ void __launch_bounds__(kTcThreads)
   // stage s is use s / kBR of raw buffer s % kBR and commit s / 2 of MMA
   // buffer s % 2, so the parities of their mbarrier phases are known
   int st_fail = nst;
-  const int m = tid;  // this thread's column
+  // this thread's column, and which half of a stage's rows it transposes
+  const int m = tid & 127, k_lo = (tid >> 7) * (kGK / 2);
   for (int st = 0; st < nst; ++st) {
     const int rb = st % kBR, cb = st & 1;
     const bool w1 = mbar_wait(&full[rb], (uint32_t)((st / kBR) & 1));  // the raw stage landed
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(kTcThreads)
     float* hi = core + cb * G::Core;
     float* lo = hi + kGTile;
 #pragma unroll
-    for (int k = 0; k < kGK; k += 4) {
+    for (int k = k_lo; k < k_lo + kGK / 2; k += 4) {
       float4 x;
       x.x = (k + 0 < nr && m < n) ? rs[(k + 0) * ldx + m] : 0.f;
       x.y = (k + 1 < nr && m < n) ? rs[(k + 1) * ldx + m] : 0.f;
@@ -414,12 +416,15 @@ __global__ void __launch_bounds__(kTcThreads)
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   __syncthreads();
   float* out = partial + (int64_t)blockIdx.x * (128 * 128);
-  const int row = warp * 32 + lane;
+  // warps w and w + 4 read lane quarter w % 4 of tensor memory, each half of
+  // the 16-column chunks
+  const int q4 = warp & 3, row = q4 * 32 + lane;
+  const int nch = (n + 15) >> 4, ch_mid = (nch + 1) >> 1;
   const bool have = ok && nst > 0;
-  for (int c0 = 0; c0 < n; c0 += 16) {
+  for (int c0 = (warp < 4 ? 0 : ch_mid) * 16; c0 < (warp < 4 ? ch_mid : nch) * 16; c0 += 16) {
     float v[16];
     if (have) {
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c0, v);
     } else {
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = 0.f;
@@ -637,82 +642,114 @@ __global__ void k_cross_reduce(const float* __restrict__ partial, int nchunks, i
 
 // ----------------------------------------------------------------- X * T
 // Y[rows, 0:kout] = X[rows, 0:n] T (T: n x kout, row-major). T^T (Np x Kp,
-// n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA. 128-row tiles
-// of X go through two cp.async buffers: the next tile is in flight while the
-// current one is multiplied (Kp / 8 MMAs) and written back from tensor memory
-// (one row per thread). VEC: X rows start 16-byte aligned (ldx % 4 == 0), so
-// each 16-byte core row is one copy; otherwise element by element.
-template <bool VEC>
-__global__ void __launch_bounds__(kTcThreads)
-    k_tc_gemm(const float* __restrict__ X, int ldx, int n, int64_t rows,
+// n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA. Each CTA
+// owns one contiguous range of rows_per_cta rows, cut into 128-row tiles
+// that go through NB cp.async buffers: the first NB tiles are all requested
+// before the first MMA (at the C2 shape, 50,000 rows of l = 100 on 152 SMs,
+// that is the CTA's whole range), and a buffer takes the tile NB further on
+// once the MMAs that read it have completed. Each tile is multiplied (Kp / 8
+// MMAs) and written back from tensor memory while the later tiles are still
+// landing. Eight warps: the index arithmetic of the copies has no divisions,
+// and in the write-back warps w and w + 4 share the 32 rows of tensor-memory
+// lane quarter w % 4, each taking half of the columns. VEC: X rows start
+// 16-byte aligned (ldx % 4 == 0), so each 16-byte core row is one copy;
+// otherwise element by element. Rows past the range are zero-filled and not
+// written.
+constexpr int kGemmThreads = 256;
+constexpr size_t kGemmSmemMax = 220 * 1024;  // dynamic shared memory of one k_tc_gemm CTA
+
+template <bool VEC, int NB>
+__global__ void __launch_bounds__(kGemmThreads)
+    k_tc_gemm(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_cta,
               const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
               int ldy, __half* __restrict__ Yh, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
-  float* Bs = smem;  // Np x Kp, then two 128 x Kp tiles of X
+  float* Bs = smem;  // Np x Kp, then NB tiles of 128 x Kp
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int kc_n = Kp >> 2;  // 16-byte chunks along K
+  const int kc_n = Kp >> 2;  // 16-byte chunks along K (at most 32)
   const uint32_t sB = smem_u32(Bs);
   const uint32_t sA0 = sB + (uint32_t)(Np * Kp) * 4u;
   const uint32_t tile_bytes = (uint32_t)(128 * Kp) * 4u;
+  const int64_t r_beg = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(rows, r_beg + rows_per_cta);
+  const int ntile = r_end > r_beg ? (int)((r_end - r_beg + 127) / 128) : 0;
   if (warp == 0) tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::);
   }
-  // B(j, k) = T[k][j]: consecutive threads take consecutive j (coalesced)
-  for (int i = tid; i < Np * Kp; i += kTcThreads) {
-    const int j = i % Np, k = i / Np;
-    const bool ok = k < n && j < kout;
-    cp_async4(sB + (uint32_t)core_off(j, k, Kp) * 4u, ok ? (const void*)(T + (int64_t)k * kout + j) : T,
-              ok ? 4u : 0u);
-  }
-  auto issue = [&](int64_t t, int buf) {
-    const int64_t row0 = t * 128;
-    const uint32_t dst = sA0 + (uint32_t)buf * tile_bytes;
+  auto issue = [&](int t) {  // tile t of this CTA into buffer t % NB
+    const int64_t row0 = r_beg + (int64_t)t * 128;
+    const uint32_t dst = sA0 + (uint32_t)(t % NB) * tile_bytes;
     if (VEC) {
-      // eight consecutive threads fill one core matrix (8 rows x 16 bytes)
-      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
-        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
-        const int64_t g = row0 + r;
-        const int k = kc * 4;
-        const int nval = g < rows ? max(0, min(4, n - k)) : 0;
-        cp_async16(dst + (uint32_t)core_off(r, k, Kp) * 4u,
-                   nval > 0 ? (const void*)(X + g * ldx + k) : X, (uint32_t)nval * 4u);
+      // thread: row tid % 8 of each core matrix, 16-byte chunk tid / 8 along
+      // K; a warp moves 8 rows x 64 contiguous bytes into 4 core matrices
+      const int r_lo = tid & 7, kc = tid >> 3;
+      if (kc < kc_n) {
+        const int nval = max(0, min(4, n - kc * 4));
+        const float* src = X + (row0 + r_lo) * ldx + kc * 4;
+        uint32_t d = dst + (uint32_t)(kc * 128 + r_lo * 16);
+#pragma unroll 4
+        for (int rg = 0; rg < 16; ++rg, src += 8 * (int64_t)ldx, d += (uint32_t)kc_n * 128u) {
+          const bool in = row0 + rg * 8 + r_lo < r_end && nval > 0;
+          cp_async16(d, in ? (const void*)src : X, in ? (uint32_t)nval * 4u : 0u);
+        }
       }
     } else {
-      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
+      for (int i = tid; i < 128 * Kp; i += kGemmThreads) {
         const int r = i / Kp, k = i % Kp;
         const int64_t g = row0 + r;
-        const bool ok = g < rows && k < n;
+        const bool ok = g < r_end && k < n;
         cp_async4(dst + (uint32_t)core_off(r, k, Kp) * 4u, ok ? (const void*)(X + g * ldx + k) : X,
                   ok ? 4u : 0u);
       }
     }
   };
-  const int64_t ntiles = (rows + 127) / 128;
-  int64_t t = blockIdx.x;
-  if (t < ntiles) issue(t, 0);
-  cp_async_commit();  // group: B + first tile
+  // B(j, k) = T[k][j], zero past n and kout, by 4-byte asynchronous copies
+  // (joining tile 0's group): thread takes columns 4 jq..4 jq + 3 of rows
+  // k = tid / 32 + 8 i, so a warp reads 128 consecutive floats of a row
+  {
+    const int jq = tid & 31;
+    if (jq * 4 < Np) {
+      for (int k = tid >> 5; k < Kp; k += kGemmThreads / 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = jq * 4 + q;
+          const bool in = k < n && j < kout;
+          cp_async4(sB + (uint32_t)core_off(j, k, Kp) * 4u,
+                    in ? (const void*)(T + (int64_t)k * kout + j) : T, in ? 4u : 0u);
+        }
+      }
+    }
+  }
+  // one commit group per tile (empty past the last): before tile t's MMAs,
+  // t + NB groups are committed, so waiting until at most NB - 1 are pending
+  // means groups 0..t (and B) have landed
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    if (t < ntile) issue(t);
+    cp_async_commit();
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_tf32(128, Np);
   const bool vec_out = (ldy & 3) == 0 && ((uintptr_t)Y & 15) == 0;
+  const int nch = Np >> 4, ch_mid = (nch + 1) >> 1;
+  const int ch_lo = warp < 4 ? 0 : ch_mid, ch_hi = warp < 4 ? ch_mid : nch;
+  const int q4 = warp & 3;  // tensor-memory lane quarter of this warp
   uint32_t phase = 0;
   bool ok = true;
-  for (int buf = 0; t < ntiles; t += gridDim.x, buf ^= 1) {
-    const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) issue(tn, buf ^ 1);  // its buffer was read by MMAs already complete
-    cp_async_commit();
-    cp_async_wait<1>();  // everything but the newest group has landed
+  for (int t = 0; t < ntile; ++t) {
+    cp_async_wait<NB - 1>();
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::);
-      const uint32_t a0 = sA0 + (uint32_t)buf * tile_bytes;
+      const uint32_t a0 = sA0 + (uint32_t)(t % NB) * tile_bytes;
       for (int kk = 0; kk < Kp / 8; ++kk) {
         const uint64_t da = smem_desc(a0 + kk * 256, 128, Kp * 32);
         const uint64_t db = smem_desc(sB + kk * 256, 128, Kp * 32);
@@ -725,13 +762,16 @@ __global__ void __launch_bounds__(kTcThreads)
       break;
     }
     phase ^= 1u;
+    // the MMAs that read buffer t % NB are done: it takes tile t + NB
+    if (t + NB < ntile) issue(t + NB);
+    cp_async_commit();
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
-    const int r = warp * 32 + lane;
-    const int64_t g = t * 128 + r;
-    for (int c0 = 0; c0 < Np; c0 += 16) {
+    const int64_t g = r_beg + (int64_t)t * 128 + q4 * 32 + lane;
+    for (int ch = ch_lo; ch < ch_hi; ++ch) {
+      const int c0 = ch * 16;
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (g < rows && Yh) {  // fp16 copy only (|entries| <= 1: columns are orthonormal)
+      tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c0, v);
+      if (g < r_end && Yh) {  // fp16 copy only (|entries| <= 1: columns are orthonormal)
         __half* y = Yh + g * ldy + c0;
 #pragma unroll
         for (int j = 0; j < 16; j += 8) {
@@ -742,7 +782,7 @@ __global__ void __launch_bounds__(kTcThreads)
                                      c0 + j + 2 * q + 1 < kout ? v[j + 2 * q + 1] : 0.f);
           if (c0 + j + 8 <= ldy) *reinterpret_cast<uint4*>(&y[j]) = *reinterpret_cast<const uint4*>(h);
         }
-      } else if (g < rows) {
+      } else if (g < r_end) {
         float* y = Y + g * ldy + c0;
         if (vec_out && c0 + 16 <= kout) {
 #pragma unroll
@@ -978,10 +1018,10 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
   const bool bulk = (ldx & 3) == 0 && ldx <= 128 && ((uintptr_t)X & 15) == 0;
   if (rows > 0) {
     if (bulk && split)
-      k_tc_gram_bulk<true><<<nchunks, kTcThreads, GramBulk<true>::Smem, s>>>(
+      k_tc_gram_bulk<true><<<nchunks, kGramThreads, GramBulk<true>::Smem, s>>>(
           X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
     else if (bulk)
-      k_tc_gram_bulk<false><<<nchunks, kTcThreads, GramBulk<false>::Smem, s>>>(
+      k_tc_gram_bulk<false><<<nchunks, kGramThreads, GramBulk<false>::Smem, s>>>(
           X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
     else if (split)
       k_tc_gram<true><<<nchunks, kTcThreads, GramRing<true>::Smem, s>>>(
@@ -1032,27 +1072,27 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
     throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: fp16 output needs ld % 8 == 0, 16-byte rows"};
   const int Kp = (n + 7) & ~7;
   const int Np = (kout + 15) & ~15;
+  // buffers of 128 x Kp: as many as fit beside T^T (2 to 4)
+  const size_t b_bytes = (size_t)Np * Kp * sizeof(float), t_bytes = (size_t)128 * Kp * sizeof(float);
+  const int nb = (int)std::min<size_t>(4, (kGemmSmemMax - b_bytes) / t_bytes);
+  const size_t bytes = b_bytes + (size_t)nb * t_bytes;
   static std::atomic<unsigned> attr{0};
   int dev = 0;
   SFD_CUDA(cudaGetDevice(&dev));
-  const int max_bytes = (128 * 128 + 2 * 128 * 128) * (int)sizeof(float);  // 192 KB
   if (dev < 32 && !(attr.load() & (1u << dev))) {
-    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  max_bytes));
-    SFD_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  max_bytes));
+    for (auto f : {k_tc_gemm<true, 2>, k_tc_gemm<true, 3>, k_tc_gemm<true, 4>, k_tc_gemm<false, 2>,
+                   k_tc_gemm<false, 3>, k_tc_gemm<false, 4>})
+      SFD_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmemMax));
     attr.fetch_or(1u << dev);
   }
-  const size_t bytes = (size_t)(Np * Kp + 2 * 128 * Kp) * sizeof(float);
+  // one contiguous range of rows per CTA, at most one CTA per SM
   const int64_t ntiles = (rows + 127) / 128;
   const int grid = (int)std::min<int64_t>(ntiles, 152);
+  const int64_t rpc = (rows + grid - 1) / grid;
   const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
-  if (vec)
-    k_tc_gemm<true><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
-                                                    Yh, ws.flags);
-  else
-    k_tc_gemm<false><<<grid, kTcThreads, bytes, s>>>(X, ldx, n, rows, T, kout, Kp, Np, Y, ldy,
-                                                     Yh, ws.flags);
+  auto k = vec ? (nb >= 4 ? k_tc_gemm<true, 4> : nb == 3 ? k_tc_gemm<true, 3> : k_tc_gemm<true, 2>)
+               : (nb >= 4 ? k_tc_gemm<false, 4> : nb == 3 ? k_tc_gemm<false, 3> : k_tc_gemm<false, 2>);
+  k<<<grid, kGemmThreads, bytes, s>>>(X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, Yh, ws.flags);
   SFD_LAUNCH_CHECK();
 }
 
