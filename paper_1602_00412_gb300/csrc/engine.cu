@@ -30,7 +30,7 @@ int bits_for(int64_t d) {
 void alloc_work(DevArena& A, SegWork& w, int64_t nseg, int64_t nnz) {
   w.cap_items = (int)(nseg + nnz / kSplit + 2);
   w.cap_split = (int)std::min<int64_t>(nseg, nnz / kSplit + 1) + 1;
-  w.items = A.alloc<int2>(w.cap_items);
+  w.items = A.alloc<int4>(w.cap_items);
   w.item_slot = A.alloc<int>(w.cap_items);
   w.item_split = A.alloc<int>(w.cap_items);
   w.split_ticket = A.alloc<unsigned>(w.cap_split);

@@ -269,16 +269,16 @@ __global__ void k_count_items(const int* __restrict__ ptr, int nseg, int* __rest
 
 __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* __restrict__ item_off,
                              const int* __restrict__ slot_off, const int* __restrict__ split_off,
-                             int2* __restrict__ items, int* __restrict__ item_slot,
+                             int4* __restrict__ items, int* __restrict__ item_slot,
                              int* __restrict__ item_split, int* __restrict__ split_seg,
                              int* __restrict__ split_first, int* __restrict__ split_count) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
-  int b = ptr[s];
+  int b = ptr[s], e = ptr[s + 1];
   int k = item_off[s + 1] - item_off[s];
   int o = item_off[s];
   for (int t = 0; t < k; ++t) {
-    items[o + t] = make_int2(s, b + t * kSplit);
+    items[o + t] = make_int4(s, b + t * kSplit, min(b + (t + 1) * kSplit, e), k > 1 ? slot_off[s] + t : -1);
     item_slot[o + t] = k > 1 ? slot_off[s] + t : -1;
     item_split[o + t] = k > 1 ? split_off[s] : -1;
   }
@@ -294,18 +294,30 @@ __global__ void k_fill_items(const int* __restrict__ ptr, int nseg, const int* _
 // One warp per work item; lane l owns float4 columns l, l+32 (VPL of them).
 // Entries are read 32 at a time (coalesced) and broadcast by shuffles; U
 // gathers per lane are in flight at once.
+// Two fp32 fused multiply-adds in one instruction (fma.rn.f32x2, sm_100 and
+// later): each element is a*b + c rounded once, exactly as fmaf, so the packed
+// form changes no result; it halves the multiply-add issue of the gathers.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 template <int VPL, int U>
 __global__ void __launch_bounds__(256)
     k_spmm(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
-           const int2* __restrict__ items, const int* __restrict__ item_slot,
+           const int4* __restrict__ items, const int* __restrict__ item_slot,
            const int* __restrict__ n_items_ptr, const float4* __restrict__ X, int ldx4, int nvec,
            float4* __restrict__ Y, int ldy4, float4* __restrict__ partial) {
   int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (item >= *n_items_ptr) return;
-  int2 it = items[item];
-  int seg = it.x, beg = it.y;
-  int end = min(beg + kSplit, ptr[seg + 1]);
+  const int4 it = items[item];
+  const int seg = it.x, beg = it.y, end = it.z;
   float4 acc[VPL];
 #pragma unroll
   for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -331,16 +343,16 @@ __global__ void __launch_bounds__(256)
           for (int u = 0; u < U; ++u) xs[u] = __ldg(&X[(int64_t)cu[u] * ldx4 + vi]);
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            acc[q].x = fmaf(vu[u], xs[u].x, acc[q].x);
-            acc[q].y = fmaf(vu[u], xs[u].y, acc[q].y);
-            acc[q].z = fmaf(vu[u], xs[u].z, acc[q].z);
-            acc[q].w = fmaf(vu[u], xs[u].w, acc[q].w);
+            const float2 vv = make_float2(vu[u], vu[u]);
+            const float2 lo = ffma2(vv, make_float2(xs[u].x, xs[u].y), make_float2(acc[q].x, acc[q].y));
+            const float2 hi = ffma2(vv, make_float2(xs[u].z, xs[u].w), make_float2(acc[q].z, acc[q].w));
+            acc[q] = make_float4(lo.x, lo.y, hi.x, hi.y);
           }
         }
       }
     }
   }
-  int slot = item_slot[item];
+  const int slot = it.w;
   float4* out = slot < 0 ? Y + (int64_t)seg * ldy4 : partial + (int64_t)slot * ldy4;
 #pragma unroll
   for (int q = 0; q < VPL; ++q) {
@@ -357,15 +369,14 @@ __global__ void __launch_bounds__(256)
 template <int U>
 __global__ void __launch_bounds__(256)
     k_spmm_h(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
-             const int2* __restrict__ items, const int* __restrict__ item_slot,
+             const int4* __restrict__ items, const int* __restrict__ item_slot,
              const int* __restrict__ n_items_ptr, const uint4* __restrict__ X, int ldx8, int nv8,
              float4* __restrict__ Y, int ldy4, float4* __restrict__ partial) {
   const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
   if (item >= *n_items_ptr) return;
-  const int2 it = items[item];
-  const int seg = it.x, beg = it.y;
-  const int end = min(beg + kSplit, ptr[seg + 1]);
+  const int4 it = items[item];
+  const int seg = it.x, beg = it.y, end = it.z;
   float acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.f;
@@ -390,11 +401,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const __half2* h = reinterpret_cast<const __half2*>(&xs[u]);
+          const float2 vv = make_float2(vu[u], vu[u]);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 f = __half22float2(h[q]);
-            acc[2 * q] = fmaf(vu[u], f.x, acc[2 * q]);
-            acc[2 * q + 1] = fmaf(vu[u], f.y, acc[2 * q + 1]);
+            const float2 a = ffma2(vv, __half22float2(h[q]), make_float2(acc[2 * q], acc[2 * q + 1]));
+            acc[2 * q] = a.x;
+            acc[2 * q + 1] = a.y;
           }
         }
       }
@@ -403,7 +415,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 16);
   if (half == 0 && hl < nv8) {
-    const int slot = item_slot[item];
+    const int slot = it.w;
     float4* out = slot < 0 ? Y + (int64_t)seg * ldy4 : partial + (int64_t)slot * ldy4;
     out[2 * hl] = make_float4(acc[0], acc[1], acc[2], acc[3]);
     out[2 * hl + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(32 * kFixWarps)
 // is needed and the sum does not depend on which item finishes last.
 __global__ void __launch_bounds__(256)
     k_spmv(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ val,
-           const int2* __restrict__ items, const int* __restrict__ item_slot,
+           const int4* __restrict__ items, const int* __restrict__ item_slot,
            const int* __restrict__ item_split, const int* __restrict__ split_first,
            const int* __restrict__ split_count, unsigned* __restrict__ split_ticket,
            const int* __restrict__ n_items_ptr, const float* __restrict__ x, float* __restrict__ y,
@@ -477,11 +489,12 @@ __global__ void __launch_bounds__(256)
   const int gl = threadIdx.x & 7, lead = threadIdx.x & 31 & ~7;
   const bool live = item < n_items;
   float a = 0.f;
-  int seg = 0;
+  int seg = 0, slot = -1;
   if (live) {
-    const int2 it = items[item];
+    const int4 it = items[item];
     seg = it.x;
-    const int end = min(it.y + kSplit, ptr[seg + 1]);
+    slot = it.w;
+    const int end = it.z;
     // eight entries per lane at a time (an item of up to 64 entries, most rows
     // of a buffer, in one round), the last group predicated: their column
     // indices and values are loaded first, then the eight gathers of x are in
@@ -509,7 +522,6 @@ __global__ void __launch_bounds__(256)
   int q = -1;
   unsigned taken = 0;
   if (live && gl == 0) {
-    const int slot = item_slot[item];
     if (slot < 0) {
       y[seg] = a;
     } else {

@@ -66,7 +66,7 @@ extern unsigned long long g_kernel_launches;
 // The item and split counts stay on the device (no host round trip): kernels
 // are launched for the capacities and read the counts.
 struct SegWork {
-  int2* items = nullptr;     // (segment, begin) ; end = min(begin + kSplit, ptr[seg+1])
+  int4* items = nullptr;     // (segment, begin, end, partial slot or -1), end - begin <= kSplit
   int* item_slot = nullptr;  // -1: item covers its whole segment, else partial slot
   int* item_split = nullptr; // -1, else the split segment (index into split_*) of the item
   unsigned* split_ticket = nullptr;  // per split segment: items done (0 between launches)
