@@ -221,7 +221,7 @@ def peaks():
 # dram__bytes_write.sum averaged over the stage's launches of one ncu capture),
 # valid while csrc/k_sparse.cu hashes to the key; the ncu summary in profiles/
 # gives the command and the per-kernel figures.
-SPMM_TRAFFIC = {"53b6a74b6f9f59e0": 33.87e6, "bbaa904771a301f8": 33.87e6}
+SPMM_TRAFFIC = {"d7fcc5f40baf45b4": 33.88e6}
 
 
 def traffic_record():
