@@ -10,6 +10,8 @@
 // Every call drains the pipeline before it returns.
 #include <string.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <deque>
 #include <memory>
@@ -183,7 +185,9 @@ int close_buffer(Ctx& C) {
   SFD_CUDA(cudaMemcpyAsync(S.csr.ptr, S.ptr_host, (m + 1) * sizeof(int), cudaMemcpyHostToDevice,
                            S.stream));
   if (m >= C.ell && C.opt.mode == 0) {
-    S.build(m, C.pend_nnz);
+    int64_t max_row = 0;
+    for (int i = 0; i < m; ++i) max_row = std::max<int64_t>(max_row, C.h_ptr[i + 1] - C.h_ptr[i]);
+    S.build(m, C.pend_nnz, max_row);
     const int q = q_for(C.opt, m);
     QControl qc;
     qc.q_fixed = q;

@@ -159,9 +159,10 @@ void Slot::wait_freed() {
   }
 }
 
-void Slot::build(int m, int64_t nnz) {
+void Slot::build(int m, int64_t nnz, int64_t max_row) {
   csr.nseg = m;
   csr.nnz = nnz;
+  csr.may_split = max_row < 0 || max_row > kSplit;
   launch_check_entries(csr.idx, csr.val, nnz, (int)d, nullptr, fro2, ws.flags, stream);
   build_work(csr, stream);
   // CSC by a stable radix sort of (col, row, val) by col

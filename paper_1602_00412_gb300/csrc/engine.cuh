@@ -107,7 +107,8 @@ struct Slot {
   // the stream must not overwrite B'^T before DenseShrink has read it
   void wait_freed();
   // CSR structure + CSC copy + work lists of the buffer already in csr.{ptr,idx,val}
-  void build(int m, int64_t nnz);
+  // max_row: the longest row of the buffer when the host knows it, else -1
+  void build(int m, int64_t nnz, int64_t max_row = -1);
   // One SparseShrink attempt (Alg. 3) + Delta + VerifySpectral (Alg. 6) +
   // verdict copy; `done` is recorded at the end. With qc->predict the power
   // count comes from the network: the host waits for the first product's

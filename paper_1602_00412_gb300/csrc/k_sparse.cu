@@ -443,7 +443,20 @@ __global__ void __launch_bounds__(32 * kFixWarps)
       const int vi = lane + 32 * q;
       float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
       if (vi < nvec) {
-        for (int t = wg; t < c; t += kFixWarps) {
+        // partials t = wg, wg + 8, ... in that order; kB loads are issued
+        // before their adds (a head column has up to hundreds of partials)
+        constexpr int kB = VPL == 1 ? 8 : 4;
+        int t = wg;
+        for (; t + (kB - 1) * kFixWarps < c; t += kB * kFixWarps) {
+          float4 p[kB];
+#pragma unroll
+          for (int u = 0; u < kB; ++u) p[u] = partial[(int64_t)(f + t + u * kFixWarps) * ldy4 + vi];
+#pragma unroll
+          for (int u = 0; u < kB; ++u) {
+            a.x += p[u].x; a.y += p[u].y; a.z += p[u].z; a.w += p[u].w;
+          }
+        }
+        for (; t < c; t += kFixWarps) {
           const float4 p = partial[(int64_t)(f + t) * ldy4 + vi];
           a.x += p.x; a.y += p.y; a.z += p.z; a.w += p.w;
         }
@@ -540,7 +553,17 @@ __global__ void __launch_bounds__(256)
     __threadfence();
   }
   float b = 0.f;
-  for (int t = gl; t < c; t += 8) b += __ldcg(&partial[f + t]);
+  {  // partials gl, gl + 8, ... in that order, eight loads before their adds
+    int t = gl;
+    for (; t + 56 < c; t += 64) {
+      float pv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pv[u] = __ldcg(&partial[f + t + 8 * u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b += pv[u];
+    }
+    for (; t < c; t += 8) b += __ldcg(&partial[f + t]);
+  }
   b += __shfl_xor_sync(0xffffffffu, b, 4);
   b += __shfl_xor_sync(0xffffffffu, b, 2);
   b += __shfl_xor_sync(0xffffffffu, b, 1);
@@ -667,6 +690,7 @@ void spmm(const Csr& c, const float* X, int ldx, int k, float* Y, int ldy, float
                                         X4, ldx / 4, nvec, Y4, ldy / 4, P4);
   }
   SFD_LAUNCH_CHECK();
+  if (!c.may_split) return;  // every item covers its whole segment
   const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));
   if (nvec <= 32)
     k_spmm_fixup<1><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,
@@ -698,6 +722,7 @@ void spmm_h(const Csr& c, const __half* X, int ldx, int k, float* Y, int ldy, fl
                                      ldx / 8, nv8, (float4*)Y, ldy / 4, (float4*)partial);
   SFD_LAUNCH_CHECK();
   const int nvec = 2 * nv8;  // float4 columns written per row
+  if (!c.may_split) return;  // every item covers its whole segment
   const int g2 = std::max(1, std::min(w.cap_split, 4 * 152));
   if (nvec <= 32)
     k_spmm_fixup<1><<<g2, 32 * kFixWarps, 0, s>>>(w.split_seg, w.split_first, w.split_count,

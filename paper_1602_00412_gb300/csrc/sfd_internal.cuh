@@ -85,6 +85,10 @@ struct Csr {
   float* val = nullptr; // nnz
   int nseg = 0;
   int64_t nnz = 0;
+  // host: false only when no segment is longer than kSplit (known from the
+  // host's copy of the row pointers), so no item writes a partial row and the
+  // products skip their split fix-up launch
+  bool may_split = true;
   SegWork work;
 };
 
