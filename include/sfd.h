@@ -327,6 +327,24 @@ int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int
 int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const float* T, int32_t kout,
                 float* Y, int32_t ldy, int32_t precision);
 
+/* Failure detection of the bounded device waits (not an operation of the
+ * paper: the tensor-core stages of Alg. 1, 3 and 5 wait on mbarriers for their
+ * copies and MMAs, and every such wait gives up after an iteration limit,
+ * raising SFD_ETIMEOUT instead of hanging).
+ * sfd_set_wait_limit: the limit of each stage's first waits on the current
+ * device, process-wide: spins < 0 restores the default (2^18 tries, about one
+ * second on GB300); 0 makes
+ * every such wait give up at once, so the next tensor-core stage reports
+ * SFD_ETIMEOUT. The waits that drain a failed stage (its copies and MMAs in
+ * flight) always keep the default, so a stage that gave up still leaves
+ * nothing running. Call it only while no library work is in flight.
+ * sfd_wait_selftest: one CTA waits, with limit `spins` (< 0: the default), on
+ * an mbarrier that nothing arrives at; returns SFD_ETIMEOUT when the wait ran
+ * out (the expected outcome), SFD_OK otherwise; *ms_out (nullable) receives
+ * its duration in milliseconds. Errors: SFD_ECUDA. */
+int sfd_set_wait_limit(int64_t spins);
+int sfd_wait_selftest(int64_t spins, float* ms_out);
+
 /* Symmetric eigendecomposition used by Alg. 3 / Alg. 5: the `nwant` largest
  * eigenvalues (descending, evals[nwant]) and their eigenvectors (evecs,
  * n x nwant row-major) of the symmetric n x n matrix S (row-major), n <= 512,

@@ -24,7 +24,10 @@ namespace sfd {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr uint32_t kSpinLimit = 1u << 24;
+// A try_wait that finds its phase incomplete suspends the thread for about
+// 3.9 us on GB300 (measured with k_wait_selftest), so 2^18 tries bound a
+// wait at about one second; copies and MMAs complete within microseconds.
+constexpr uint32_t kSpinLimit = 1u << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -63,9 +66,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
       smem_u32(mbar)));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Iteration limit of the first waits of every stage (a copy landed, an MMA
+// done); sfd_set_wait_limit changes it for tests (0: such a wait gives up at
+// once). The waits that drain a failed stage (mbar_drain) keep kSpinLimit,
+// so a CTA never releases shared or tensor memory with a copy or an MMA of
+// its own still in flight.
+__device__ uint32_t g_wait_limit = kSpinLimit;
+
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* mbar, uint32_t parity, uint32_t limit) {
   uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+  for (uint32_t it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
@@ -73,6 +83,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_u32(mbar)), "r"(parity));
   }
   return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  return mbar_wait_n(mbar, parity, *(volatile uint32_t*)&g_wait_limit);
+}
+
+__device__ __forceinline__ bool mbar_drain(uint64_t* mbar, uint32_t parity) {
+  return mbar_wait_n(mbar, parity, kSpinLimit);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads)
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
     for (int b = 0; b < kGSt; ++b)  // bounded: let MMAs in flight finish before freeing
-      if (used_bits & (1u << b)) mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+      if (used_bits & (1u << b)) mbar_drain(&mbar[b], (phase_bits >> b) & 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   __syncthreads();
@@ -404,14 +422,16 @@ __global__ void __launch_bounds__(kGramThreads)
     for (int s2 = max(0, nst - 2); s2 < nst; ++s2)
       all = mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1)) && all;
     ok = __syncthreads_and(all);
-  } else {
+  }
+  if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
-    // bounded waits: the MMAs committed and the bulk copies issued finish
-    // before the shared memory and tensor memory are released
+    // draining waits: the MMAs committed and the bulk copies issued finish
+    // before the shared memory and tensor memory are released (every copy
+    // up to stage nst - 1 has landed when the loop ran to the end)
     for (int s2 = max(0, st_fail - 2); s2 < st_fail; ++s2)
-      mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1));
+      mbar_drain(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1));
     for (int s2 = st_fail; s2 < min(nst, st_fail + kBR - 1); ++s2)
-      mbar_wait(&full[s2 % kBR], (uint32_t)((s2 / kBR) & 1));
+      mbar_drain(&full[s2 % kBR], (uint32_t)((s2 / kBR) & 1));
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   __syncthreads();
@@ -439,6 +459,22 @@ __global__ void __launch_bounds__(kGramThreads)
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
   if (warp == 0) tmem_free(tmem, 128);
+}
+
+// ------------------------------------------------------- wait self-test
+// A wait that nothing ends: one CTA waits, with the given iteration limit, on
+// an mbarrier that no thread and no copy ever arrives at. The wait gives up,
+// the timeout flag is raised and the kernel returns; nothing is in flight, so
+// the context stays usable. Tests use it to see the bound work and to time it.
+__global__ void k_wait_selftest(uint32_t limit, int* __restrict__ flags) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_n(&mbar, 0u, limit);  // phase 0 never completes
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(&flags[2], 1);
 }
 
 // ----------------------------------------------------------- cross Gram
@@ -570,7 +606,7 @@ __global__ void __launch_bounds__(kTcThreads)
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
     for (int b = 0; b < kXSt; ++b)  // bounded: let MMAs in flight finish before freeing
-      if (used_bits & (1u << b)) mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+      if (used_bits & (1u << b)) mbar_drain(&mbar[b], (phase_bits >> b) & 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   __syncthreads();
@@ -801,7 +837,7 @@ __global__ void __launch_bounds__(kGemmThreads)
   cp_async_wait<0>();
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
-    mbar_wait(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
+    mbar_drain(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
@@ -940,7 +976,7 @@ __global__ void __launch_bounds__(kTcThreads)
   cp_async_wait<0>();
   if (!ok) {
     if (tid == 0) atomicOr(&flags[2], 1);
-    mbar_wait(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
+    mbar_drain(&mbar, phase);  // bounded: let an MMA in flight finish before freeing
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
@@ -1094,6 +1130,41 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
                : (nb >= 4 ? k_tc_gemm<false, 4> : nb == 3 ? k_tc_gemm<false, 3> : k_tc_gemm<false, 2>);
   k<<<grid, kGemmThreads, bytes, s>>>(X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, Yh, ws.flags);
   SFD_LAUNCH_CHECK();
+}
+
+
+void set_wait_limit(int64_t spins) {
+  const uint32_t v = spins < 0 ? kSpinLimit : (uint32_t)std::min<int64_t>(spins, kSpinLimit);
+  SFD_CUDA(cudaMemcpyToSymbol(g_wait_limit, &v, sizeof(v)));
+}
+
+int wait_selftest(int64_t spins, float* ms) {
+  const uint32_t limit = spins < 0 ? kSpinLimit : (uint32_t)std::min<int64_t>(spins, kSpinLimit);
+  int* flags = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int timed_out = 0;
+  try {
+    SFD_CUDA(cudaMalloc(&flags, 16 * sizeof(int)));
+    SFD_CUDA(cudaMemset(flags, 0, 16 * sizeof(int)));
+    SFD_CUDA(cudaEventCreate(&e0));
+    SFD_CUDA(cudaEventCreate(&e1));
+    SFD_CUDA(cudaEventRecord(e0, 0));
+    k_wait_selftest<<<1, 128>>>(limit, flags);
+    SFD_LAUNCH_CHECK();
+    SFD_CUDA(cudaEventRecord(e1, 0));
+    SFD_CUDA(cudaEventSynchronize(e1));
+    if (ms) SFD_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    SFD_CUDA(cudaMemcpy(&timed_out, flags + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (flags) cudaFree(flags);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(flags);
+  return timed_out;
 }
 
 }  // namespace sfd

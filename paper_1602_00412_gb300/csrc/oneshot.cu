@@ -260,6 +260,23 @@ int sfd_orthonormalize(int64_t rows, int32_t k, float* X, int32_t ld) {
   }
 }
 
+int sfd_set_wait_limit(int64_t spins) {
+  try {
+    set_wait_limit(spins);
+    return SFD_OK;
+  } catch (const CudaError& e) {
+    return code_of(e);
+  }
+}
+
+int sfd_wait_selftest(int64_t spins, float* ms_out) {
+  try {
+    return wait_selftest(spins, ms_out) ? SFD_ETIMEOUT : SFD_OK;
+  } catch (const CudaError& e) {
+    return code_of(e);
+  }
+}
+
 int sfd_gram(int64_t rows, int32_t k, const float* X, int32_t ldx, float* G, int32_t precision) {
   if (rows < 0 || k < 1 || k > kMaxEll || ldx < k || !G || (rows > 0 && !X)) return SFD_EINVAL;
   if (precision != 0 && !((precision == 1 || precision == 2) && tc_supported(k, k)))

@@ -54,7 +54,8 @@ EXPORTS = ["sfd_options_init", "sfd_create", "sfd_append_rows", "sfd_sketch", "s
            "sfd_get_stats", "sfd_reset", "sfd_destroy", "sfd_strerror", "sfd_last_error", "sfd_bssh_buffer",
            "sfd_dense_shrink", "sfd_csr_spmm", "sfd_spmm_variant_count", "sfd_csr_spmm_ex",
            "sfd_orthonormalize", "sfd_symeig",
-           "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_q_model", "sfd_q_log",
+           "sfd_symeig_noalloc", "sfd_gram", "sfd_gemm_ts", "sfd_set_wait_limit", "sfd_wait_selftest",
+           "sfd_set_q_model", "sfd_q_log",
            "sfd_q_features", "sfd_q_predict", "sfd_q_grad", "sfd_q_train", "sfd_batch_create",
            "sfd_batch_append", "sfd_batch_wait", "sfd_batch_sketch", "sfd_batch_merge_tree",
            "sfd_batch_stats", "sfd_batch_destroy", "sfd_save", "sfd_load"]
@@ -99,6 +100,8 @@ def load(path=None):
     L.sfd_symeig_noalloc.argtypes = [i32, vp, i32, vp, vp]
     L.sfd_gram.argtypes = [i64, i32, vp, i32, vp, i32]
     L.sfd_gemm_ts.argtypes = [i64, i32, vp, i32, vp, i32, vp, i32, i32]
+    L.sfd_set_wait_limit.argtypes = [i64]
+    L.sfd_wait_selftest.argtypes = [i64, ctypes.POINTER(ctypes.c_float)]
     L.sfd_set_q_model.argtypes = [vp, vp]
     L.sfd_q_log.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(i64)]
     L.sfd_q_features.argtypes = [i64, i64, i32, vp, vp, vp, u64, i64, i32, vp]
@@ -277,6 +280,21 @@ def sfd_orthonormalize(rows, k, X, ld):
 def sfd_gram(rows, k, X, ldx, G, precision=0):
     _check(load().sfd_gram(rows, k, ctypes.c_void_p(X.data_ptr()), ldx,
                            ctypes.c_void_p(G.data_ptr()), int(precision)))
+
+
+def sfd_set_wait_limit(spins):
+    """Iteration limit of the tensor-core stages' first waits (< 0: the default;
+    0: they give up at once and the stage reports SFD_ETIMEOUT)."""
+    _check(load().sfd_set_wait_limit(int(spins)))
+
+
+def sfd_wait_selftest(spins):
+    """Run one bounded wait that nothing ends; returns (status, milliseconds)."""
+    ms = ctypes.c_float(0.0)
+    rc = load().sfd_wait_selftest(int(spins), ctypes.byref(ms))
+    if rc not in (SFD_OK, SFD_ETIMEOUT):
+        _check(rc)
+    return rc, ms.value
 
 
 def sfd_gemm_ts(rows, n, X, ldx, T, kout, Y, ldy, precision=0):
