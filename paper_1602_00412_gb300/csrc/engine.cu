@@ -378,7 +378,17 @@ void Merger::dense_shrink(const float* Xt, int ldx, int k1, bool orthogonal_rows
     gram(Bt[cur], ld, map, d, ws.small_a, ws, stream);
   symeig(ws.small_a, n, ell, ws.evals, ws.small_b, ws.eig_work, stream, true);
   shrink_weights(ws.evals, ws.small_b, n, ell, ell, 0, ws.small_a, ws.scalars, stream);
-  gemm_ts(Bt[cur], ld, map, d, ws.small_a, ell, Bt[1 - cur], ld, stream);
+  // B^T <- M^T T with M^T = [B^T | X^T] (T: n x l, row-major): in mixed
+  // precision as B^T T[0:l] + X^T T[l:n] on the tensor cores (split TF32,
+  // each block within one K tile), else in FP32 on the CUDA cores
+  if (mixed && k1 >= 1 && tc_split_supported(ell, ell) && tc_split_supported(k1, ell)) {
+    gemm_ts_tc(Bt[cur], ld, single_map(ell), d, ws.small_a, ell, Bt[1 - cur], ld, ws, stream,
+               nullptr, true);
+    gemm_ts_tc(Xt, ldx, single_map(k1), d, ws.small_a + (size_t)ell * ell, ell, Bt[1 - cur], ld,
+               ws, stream, nullptr, true, true);
+  } else {
+    gemm_ts(Bt[cur], ld, map, d, ws.small_a, ell, Bt[1 - cur], ld, stream);
+  }
   cur = 1 - cur;
 }
 

@@ -849,11 +849,13 @@ __global__ void __launch_bounds__(kGemmThreads)
 // X_hi T_hi + X_hi T_lo + X_lo T_hi (about 21 significant bits). One A tile
 // in flight (hi and lo of both operands take the shared memory); each thread
 // splits the elements it copied itself.
+constexpr int kGemm3MaxNp = 112;  // the split form's widest output (kout <= 112)
+
 template <bool VEC>
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_gemm3(const float* __restrict__ X, int ldx, int n, int64_t rows,
                const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
-               int ldy, int* __restrict__ flags) {
+               int ldy, bool accumulate, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
   float* Bh = smem;                  // Np x Kp
   float* Bl = Bh + Np * Kp;          // Np x Kp
@@ -946,27 +948,50 @@ __global__ void __launch_bounds__(kTcThreads)
       }
       mma_commit(&mbar);
     }
+    // accumulate: this thread's row of Y is requested while the MMAs run
+    // (vec_out holds: the host requires it), so the adds do not wait on it
+    const int r = warp * 32 + lane;
+    const int64_t g = row0 + r;
+    float4 yold[kGemm3MaxNp / 4];
+    if (accumulate) {
+#pragma unroll
+      for (int q = 0; q < kGemm3MaxNp / 4; ++q)
+        yold[q] = g < rows && 4 * q < kout ? *reinterpret_cast<const float4*>(Y + g * ldy + 4 * q)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
       ok = false;
       break;
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
-    const int r = warp * 32 + lane;
-    const int64_t g = row0 + r;
-    for (int c0 = 0; c0 < Np; c0 += 16) {
+#pragma unroll
+    for (int ch = 0; ch < kGemm3MaxNp / 16; ++ch) {
+      const int c0 = ch * 16;
+      if (c0 >= Np) break;
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
       if (g < rows) {
         float* y = Y + g * ldy + c0;
         if (vec_out && c0 + 16 <= kout) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4*>(&y[j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          for (int j = 0; j < 16; j += 4) {
+            float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            if (accumulate) {
+              const float4 p = yold[(c0 + j) / 4];
+              o = make_float4(p.x + o.x, p.y + o.y, p.z + o.z, p.w + o.w);
+            }
+            *reinterpret_cast<float4*>(&y[j]) = o;
+          }
         } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < kout) y[j] = v[j];
+          for (int j = 0; j < 16; ++j) {
+            if (c0 + j < kout) {
+              const float4 p = yold[(c0 + j) / 4];
+              const float pj = (j & 3) == 0 ? p.x : (j & 3) == 1 ? p.y : (j & 3) == 2 ? p.z : p.w;
+              y[j] = accumulate ? pj + v[j] : v[j];
+            }
+          }
         }
       }
     }
@@ -1073,9 +1098,13 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
 }
 
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
-                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh, bool split) {
+                float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh, bool split,
+                bool accumulate) {
   if (rows <= 0 || kout <= 0) return;
   const int n = map.total();
+  if (accumulate && (!split || (ldy & 3) || ((uintptr_t)Y & 15)))
+    throw CudaError{cudaErrorInvalidValue,
+                    "gemm_ts_tc: accumulation in the split form, Y rows 16-byte aligned"};
   if (split) {
     if (!tc_split_supported(n, kout) || map.k1 != 0 || Yh)
       throw CudaError{cudaErrorInvalidValue, "gemm_ts_tc: split form needs n, kout <= 112"};
@@ -1095,10 +1124,12 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
     const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
     if (vec)
       k_tc_gemm3<true><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
-                                                                     Np, Y, ldy, ws.flags);
+                                                                     Np, Y, ldy, accumulate,
+                                                                     ws.flags);
     else
       k_tc_gemm3<false><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
-                                                                      Np, Y, ldy, ws.flags);
+                                                                      Np, Y, ldy, accumulate,
+                                                                      ws.flags);
     SFD_LAUNCH_CHECK();
     return;
   }

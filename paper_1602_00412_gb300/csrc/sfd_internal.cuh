@@ -203,9 +203,10 @@ void cross_gram_tc(const float* X1, int ld1, int n1, const float* X2, int ld2, i
                    int64_t rows, float* G, Workspace& ws, cudaStream_t s);
 // Yh (optional): write Y as fp16 into Yh (ld ldy, a multiple of 8, >= kout;
 // columns kout..ldy-1 get 0) instead of fp32 into Y; for |entries| <= 1.
+// accumulate (split form only): Y += X T instead of Y = X T.
 void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* T, int kout,
                 float* Y, int ldy, Workspace& ws, cudaStream_t s, __half* Yh = nullptr,
-                bool split = false);
+                bool split = false, bool accumulate = false);
 // Cholesky of G + shift (k x k) and the inverse of the factor: Rinv (k x k
 // row-major, upper triangular) with G + shift = R^T R. flags[1] counts pivots
 // clamped. fp64: factorisation and inverse in double (one CTA; work holds
