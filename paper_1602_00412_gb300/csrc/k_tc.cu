@@ -846,14 +846,24 @@ __global__ void __launch_bounds__(kGemmThreads)
 
 // Y[rows, 0:kout] = X[rows, 0:n] T in the split form: X and T^T are split
 // into TF32 hi and lo parts in shared memory and Y accumulates
-// X_hi T_hi + X_hi T_lo + X_lo T_hi (about 21 significant bits). One A tile
-// in flight (hi and lo of both operands take the shared memory); each thread
-// splits the elements it copied itself.
-constexpr int kGemm3MaxNp = 112;  // the split form's widest output (kout <= 112)
+// X_hi T_hi + X_hi T_lo + X_lo T_hi (about 21 significant bits). Each CTA owns
+// one contiguous range of rows, in 128-row tiles. One A tile is staged at a
+// time (hi and lo of both operands fill the shared memory), but the next
+// tile's rows are requested as soon as the MMAs of the current one have
+// completed, so they land while the current tile is written back from tensor
+// memory. The splits are elementwise over whole buffers (the hi and lo
+// buffers share one layout). Eight warps: warps w and w + 4 share tensor
+// memory lane quarter w % 4, each writing half of the columns. accumulate:
+// Y += X T, the old rows of Y requested while the MMAs run (Y rows 16-byte
+// aligned, checked by the host).
+// the split form's outputs are at most 112 wide: 7 chunks of 16 columns, at
+// most 4 per warp half (the yold registers below)
+constexpr int kGemm3MaxNp = 112;
+static_assert((kGemm3MaxNp / 16 + 1) / 2 <= 4, "k_tc_gemm3: 4 chunks per warp half");
 
 template <bool VEC>
-__global__ void __launch_bounds__(kTcThreads)
-    k_tc_gemm3(const float* __restrict__ X, int ldx, int n, int64_t rows,
+__global__ void __launch_bounds__(kGemmThreads)
+    k_tc_gemm3(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_cta,
                const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
                int ldy, bool accumulate, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
@@ -864,73 +874,83 @@ __global__ void __launch_bounds__(kTcThreads)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int kc_n = Kp >> 2;
+  const int kc_n = Kp >> 2;  // 16-byte chunks along K (at most 28)
+  const int64_t r_beg = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(rows, r_beg + rows_per_cta);
+  const int ntile = r_end > r_beg ? (int)((r_end - r_beg + 127) / 128) : 0;
   if (warp == 0) tmem_alloc(&tmem_slot, 128);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::);
   }
-  for (int i = tid; i < Np * Kp; i += kTcThreads) {  // B(j, k) = T[k][j]
-    const int j = i % Np, k = i / Np;
-    const bool ok = k < n && j < kout;
-    cp_async4(smem_u32(Bh) + (uint32_t)core_off(j, k, Kp) * 4u,
-              ok ? (const void*)(T + (int64_t)k * kout + j) : T, ok ? 4u : 0u);
+  auto issue = [&](int t) {  // tile t of this CTA, raw, into Ah
+    const int64_t row0 = r_beg + (int64_t)t * 128;
+    const uint32_t dst = smem_u32(Ah);
+    if (VEC) {
+      const int r_lo = tid & 7, kc = tid >> 3;
+      if (kc < kc_n) {
+        const int nval = max(0, min(4, n - kc * 4));
+        const float* src = X + (row0 + r_lo) * ldx + kc * 4;
+        uint32_t d = dst + (uint32_t)(kc * 128 + r_lo * 16);
+#pragma unroll 4
+        for (int rg = 0; rg < 16; ++rg, src += 8 * (int64_t)ldx, d += (uint32_t)kc_n * 128u) {
+          const bool in = row0 + rg * 8 + r_lo < r_end && nval > 0;
+          cp_async16(d, in ? (const void*)src : X, in ? (uint32_t)nval * 4u : 0u);
+        }
+      }
+    } else {
+      for (int i = tid; i < 128 * Kp; i += kGemmThreads) {
+        const int r = i / Kp, k = i % Kp;
+        const int64_t g = row0 + r;
+        const bool okk = g < r_end && k < n;
+        cp_async4(dst + (uint32_t)core_off(r, k, Kp) * 4u, okk ? (const void*)(X + g * ldx + k) : X,
+                  okk ? 4u : 0u);
+      }
+    }
+  };
+  {  // B(j, k) = T[k][j], zero past n and kout (a warp reads 128 floats of a row of T)
+    const int jq = tid & 31;
+    if (jq * 4 < Np) {
+      for (int k = tid >> 5; k < Kp; k += kGemmThreads / 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = jq * 4 + q;
+          const bool in = k < n && j < kout;
+          cp_async4(smem_u32(Bh) + (uint32_t)core_off(j, k, Kp) * 4u,
+                    in ? (const void*)(T + (int64_t)k * kout + j) : T, in ? 4u : 0u);
+        }
+      }
+    }
   }
+  if (ntile > 0) issue(0);
   cp_async_commit();
-  cp_async_wait<0>();
-  for (int i = tid; i < Np * Kp; i += kTcThreads) {
-    const int o = core_off(i % Np, i / Np, Kp);
-    const float x = Bh[o], h = tf32_hi(x);
-    Bh[o] = h;
-    Bl[o] = x - h;
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::);
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_tf32(128, Np);
-  const int64_t ntiles = (rows + 127) / 128;
   const bool vec_out = (ldy & 3) == 0 && ((uintptr_t)Y & 15) == 0;
+  const int nch = Np >> 4, ch_mid = (nch + 1) >> 1;
+  const int ch_lo = warp < 4 ? 0 : ch_mid, ch_hi = warp < 4 ? ch_mid : nch;
+  const int q4 = warp & 3;
   uint32_t phase = 0;
   bool ok = true;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t row0 = t * 128;
-    if (VEC) {
-      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
-        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
-        const int64_t g = row0 + r;
-        const int k = kc * 4;
-        const int nval = g < rows ? max(0, min(4, n - k)) : 0;
-        cp_async16(smem_u32(Ah) + (uint32_t)core_off(r, k, Kp) * 4u,
-                   nval > 0 ? (const void*)(X + g * ldx + k) : X, (uint32_t)nval * 4u);
-      }
-    } else {
-      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
-        const int r = i / Kp, k = i % Kp;
-        const int64_t g = row0 + r;
-        const bool okk = g < rows && k < n;
-        cp_async4(smem_u32(Ah) + (uint32_t)core_off(r, k, Kp) * 4u,
-                  okk ? (const void*)(X + g * ldx + k) : X, okk ? 4u : 0u);
+  for (int t = 0; t < ntile; ++t) {
+    cp_async_wait<0>();  // this thread's copies of tile t (and, first, of B)
+    __syncthreads();
+    if (t == 0) {
+      for (int i = tid; i < (Np * Kp) >> 2; i += kGemmThreads) {
+        const float4 x = reinterpret_cast<const float4*>(Bh)[i];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        reinterpret_cast<float4*>(Bh)[i] = h;
+        reinterpret_cast<float4*>(Bl)[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
       }
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    if (VEC) {
-      for (int i = tid; i < 128 * kc_n; i += kTcThreads) {
-        const int r = (i & 7) + ((i >> 3) / kc_n) * 8, kc = (i >> 3) % kc_n;
-        const int o = core_off(r, kc * 4, Kp);
-        const float4 x = *reinterpret_cast<const float4*>(Ah + o);
-        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-        *reinterpret_cast<float4*>(Ah + o) = h;
-        *reinterpret_cast<float4*>(Al + o) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-    } else {
-      for (int i = tid; i < 128 * Kp; i += kTcThreads) {
-        const int o = core_off(i / Kp, i % Kp, Kp);
-        const float x = Ah[o], h = tf32_hi(x);
-        Ah[o] = h;
-        Al[o] = x - h;
-      }
+    for (int i = tid; i < (128 * Kp) >> 2; i += kGemmThreads) {
+      const float4 x = reinterpret_cast<const float4*>(Ah)[i];
+      const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+      reinterpret_cast<float4*>(Ah)[i] = h;
+      reinterpret_cast<float4*>(Al)[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::);
     __syncthreads();
@@ -948,37 +968,43 @@ __global__ void __launch_bounds__(kTcThreads)
       }
       mma_commit(&mbar);
     }
-    // accumulate: this thread's row of Y is requested while the MMAs run
-    // (vec_out holds: the host requires it), so the adds do not wait on it
-    const int r = warp * 32 + lane;
-    const int64_t g = row0 + r;
-    float4 yold[kGemm3MaxNp / 4];
+    const int64_t g = r_beg + (int64_t)t * 128 + q4 * 32 + lane;
+    float4 yold[16];  // this thread's old values, up to four 16-column chunks
     if (accumulate) {
 #pragma unroll
-      for (int q = 0; q < kGemm3MaxNp / 4; ++q)
-        yold[q] = g < rows && 4 * q < kout ? *reinterpret_cast<const float4*>(Y + g * ldy + 4 * q)
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < 4; ++i) {
+        const int c0 = (ch_lo + i) * 16;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          yold[4 * i + j] = g < r_end && ch_lo + i < ch_hi && c0 + 4 * j < kout
+                                ? *reinterpret_cast<const float4*>(Y + g * ldy + c0 + 4 * j)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
       ok = false;
       break;
     }
     phase ^= 1u;
+    // the MMAs read A: its buffers take the next tile while this one is written back
+    if (t + 1 < ntile) issue(t + 1);
+    cp_async_commit();
     asm volatile("tcgen05.fence::after_thread_sync;" ::);
 #pragma unroll
-    for (int ch = 0; ch < kGemm3MaxNp / 16; ++ch) {
+    for (int i = 0; i < 4; ++i) {
+      const int ch = ch_lo + i;
+      if (ch >= ch_hi) break;
       const int c0 = ch * 16;
-      if (c0 >= Np) break;
       float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (g < rows) {
+      tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + c0, v);
+      if (g < r_end) {
         float* y = Y + g * ldy + c0;
         if (vec_out && c0 + 16 <= kout) {
 #pragma unroll
           for (int j = 0; j < 16; j += 4) {
             float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             if (accumulate) {
-              const float4 p = yold[(c0 + j) / 4];
+              const float4 p = yold[4 * i + j / 4];
               o = make_float4(p.x + o.x, p.y + o.y, p.z + o.z, p.w + o.w);
             }
             *reinterpret_cast<float4*>(&y[j]) = o;
@@ -987,16 +1013,19 @@ __global__ void __launch_bounds__(kTcThreads)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (c0 + j < kout) {
-              const float4 p = yold[(c0 + j) / 4];
-              const float pj = (j & 3) == 0 ? p.x : (j & 3) == 1 ? p.y : (j & 3) == 2 ? p.z : p.w;
-              y[j] = accumulate ? pj + v[j] : v[j];
+              float o = v[j];
+              if (accumulate) {
+                const float4 p = yold[4 * i + j / 4];
+                o += (j & 3) == 0 ? p.x : (j & 3) == 1 ? p.y : (j & 3) == 2 ? p.z : p.w;
+              }
+              y[j] = o;
             }
           }
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::);
-    __syncthreads();  // tensor memory and the A tile are free for the next tile
+    __syncthreads();  // tensor memory is free for the next tile's MMAs
   }
   cp_async_wait<0>();
   if (!ok) {
@@ -1119,17 +1148,17 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
       attr3.fetch_or(1u << dv);
     }
     const int Kp = (n + 7) & ~7, Np = (kout + 15) & ~15;
+    // one contiguous range of rows per CTA, at most one CTA per SM
     const int64_t ntiles = (rows + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, 152);
+    const int64_t rpc = (rows + grid - 1) / grid;
     const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
     if (vec)
-      k_tc_gemm3<true><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
-                                                                     Np, Y, ldy, accumulate,
-                                                                     ws.flags);
+      k_tc_gemm3<true><<<grid, kGemmThreads, gemm3_smem(n, kout), s>>>(
+          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, ws.flags);
     else
-      k_tc_gemm3<false><<<grid, kTcThreads, gemm3_smem(n, kout), s>>>(X, ldx, n, rows, T, kout, Kp,
-                                                                      Np, Y, ldy, accumulate,
-                                                                      ws.flags);
+      k_tc_gemm3<false><<<grid, kGemmThreads, gemm3_smem(n, kout), s>>>(
+          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, ws.flags);
     SFD_LAUNCH_CHECK();
     return;
   }
