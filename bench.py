@@ -221,7 +221,7 @@ def peaks():
 # dram__bytes_write.sum averaged over the stage's launches of one ncu capture),
 # valid while csrc/k_sparse.cu hashes to the key; the ncu summary in profiles/
 # gives the command and the per-kernel figures.
-SPMM_TRAFFIC = {"d7fcc5f40baf45b4": 33.88e6}
+SPMM_TRAFFIC = {"6fbc0266d65e63bf": 33.85e6}
 
 
 def traffic_record():

@@ -66,12 +66,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
       smem_u32(mbar)));
 }
 
-// Iteration limit of the first waits of every stage (a copy landed, an MMA
-// done); sfd_set_wait_limit changes it for tests (0: such a wait gives up at
-// once). The waits that drain a failed stage (mbar_drain) keep kSpinLimit,
-// so a CTA never releases shared or tensor memory with a copy or an MMA of
-// its own still in flight.
-__device__ uint32_t g_wait_limit = kSpinLimit;
+// The first waits of every stage (a copy landed, an MMA done) take their
+// iteration limit as a kernel argument (wl), kSpinLimit unless
+// sfd_set_wait_limit changed it for tests (0: such a wait gives up at once).
+// The waits that drain a failed stage (mbar_drain) keep kSpinLimit, so a CTA
+// never releases shared or tensor memory with a copy or an MMA of its own
+// still in flight.
 
 __device__ __forceinline__ bool mbar_wait_n(uint64_t* mbar, uint32_t parity, uint32_t limit) {
   uint32_t done = 0;
@@ -85,8 +85,8 @@ __device__ __forceinline__ bool mbar_wait_n(uint64_t* mbar, uint32_t parity, uin
   return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  return mbar_wait_n(mbar, parity, *(volatile uint32_t*)&g_wait_limit);
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+  return mbar_wait_n(mbar, parity, limit);
 }
 
 __device__ __forceinline__ bool mbar_drain(uint64_t* mbar, uint32_t parity) {
@@ -162,7 +162,7 @@ __device__ __forceinline__ float tf32_hi(float x) {
 template <bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_gram(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_chunk,
-              float* __restrict__ partial, int* __restrict__ flags) {
+              float* __restrict__ partial, uint32_t wl, int* __restrict__ flags) {
   constexpr int kGSt = GramRing<SPLIT>::St;
   constexpr int kGLook = GramRing<SPLIT>::Look;
   extern __shared__ __align__(1024) float smem[];
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kTcThreads)
     if (ns < nst) {
       const int b = ns % kGSt;
       if (used_bits & (1u << b)) {  // the MMAs that read this buffer must be done
-        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u, wl);
         if (!__syncthreads_and(w)) { ok = false; break; }
         phase_bits ^= 1u << b;
         used_bits &= ~(1u << b);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kTcThreads)
     // mbarrier arrival can land after the CTA has released its shared memory
     bool all = true;
     for (int b = 0; b < kGSt; ++b)
-      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u) && all;
+      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u, wl) && all;
     ok = __syncthreads_and(all);
     if (ok) used_bits = 0;
   }
@@ -329,7 +329,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 template <bool SPLIT>
 __global__ void __launch_bounds__(kGramThreads)
     k_tc_gram_bulk(const float* __restrict__ X, int ldx, int n, int64_t rows,
-                   int64_t rows_per_chunk, float* __restrict__ partial, int* __restrict__ flags) {
+                   int64_t rows_per_chunk, float* __restrict__ partial, uint32_t wl, int* __restrict__ flags) {
   using G = GramBulk<SPLIT>;
   extern __shared__ __align__(1024) float smem[];
   float* raw = smem;                  // kBR x (kGK x ldx), row-major as in memory
@@ -372,9 +372,9 @@ __global__ void __launch_bounds__(kGramThreads)
   const int m = tid & 127, k_lo = (tid >> 7) * (kGK / 2);
   for (int st = 0; st < nst; ++st) {
     const int rb = st % kBR, cb = st & 1;
-    const bool w1 = mbar_wait(&full[rb], (uint32_t)((st / kBR) & 1));  // the raw stage landed
+    const bool w1 = mbar_wait(&full[rb], (uint32_t)((st / kBR) & 1), wl);  // the raw stage landed
     // the MMAs of stage st - 2, which read this MMA buffer, are done
-    const bool w2 = st < 2 || mbar_wait(&mmad[cb], (uint32_t)(((st - 2) >> 1) & 1));
+    const bool w2 = st < 2 || mbar_wait(&mmad[cb], (uint32_t)(((st - 2) >> 1) & 1), wl);
     if (!__syncthreads_and(w1 && w2)) { st_fail = st; break; }
     const int nr = (int)min((int64_t)kGK, r_end - (r_beg + (int64_t)st * kGK));
     const float* rs = raw + rb * G::Raw;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kGramThreads)
   if (ok) {
     bool all = true;  // the last commit of each MMA buffer
     for (int s2 = max(0, nst - 2); s2 < nst; ++s2)
-      all = mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1)) && all;
+      all = mbar_wait(&mmad[s2 & 1], (uint32_t)((s2 >> 1) & 1), wl) && all;
     ok = __syncthreads_and(all);
   }
   if (!ok) {
@@ -496,7 +496,7 @@ constexpr int kXPartial = 128 * 128 + 256;                      // floats per ch
 __global__ void __launch_bounds__(kTcThreads)
     k_tc_cross(const float* __restrict__ X1, int ld1, int n1, const float* __restrict__ X2,
                int ld2, int n2, int64_t rows, int64_t rows_per_chunk, float* __restrict__ partial,
-               int* __restrict__ flags) {
+               uint32_t wl, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
   __shared__ __align__(8) uint64_t mbar[kXSt];
   __shared__ uint32_t tmem_slot;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(kTcThreads)
     if (ns < nst) {
       const int b = ns % kXSt;
       if (used_bits & (1u << b)) {  // the MMAs that read this buffer must be done
-        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u);
+        const bool w = mbar_wait(&mbar[b], (phase_bits >> b) & 1u, wl);
         if (!__syncthreads_and(w)) { ok = false; break; }
         phase_bits ^= 1u << b;
         used_bits &= ~(1u << b);
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kTcThreads)
   if (ok) {
     bool all = true;
     for (int b = 0; b < kXSt; ++b)
-      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u) && all;
+      if (used_bits & (1u << b)) all = mbar_wait(&mbar[b], (phase_bits >> b) & 1u, wl) && all;
     ok = __syncthreads_and(all);
     if (ok) used_bits = 0;
   }
@@ -698,7 +698,7 @@ template <bool VEC, int NB>
 __global__ void __launch_bounds__(kGemmThreads)
     k_tc_gemm(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_cta,
               const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
-              int ldy, __half* __restrict__ Yh, int* __restrict__ flags) {
+              int ldy, __half* __restrict__ Yh, uint32_t wl, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
   float* Bs = smem;  // Np x Kp, then NB tiles of 128 x Kp
   __shared__ __align__(8) uint64_t mbar;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       }
       mma_commit(&mbar);
     }
-    if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
+    if (!__syncthreads_and(mbar_wait(&mbar, phase, wl))) {
       ok = false;
       break;
     }
@@ -865,7 +865,7 @@ template <bool VEC>
 __global__ void __launch_bounds__(kGemmThreads)
     k_tc_gemm3(const float* __restrict__ X, int ldx, int n, int64_t rows, int64_t rows_per_cta,
                const float* __restrict__ T, int kout, int Kp, int Np, float* __restrict__ Y,
-               int ldy, bool accumulate, int* __restrict__ flags) {
+               int ldy, bool accumulate, uint32_t wl, int* __restrict__ flags) {
   extern __shared__ __align__(1024) float smem[];
   float* Bh = smem;                  // Np x Kp
   float* Bl = Bh + Np * Kp;          // Np x Kp
@@ -981,7 +981,7 @@ __global__ void __launch_bounds__(kGemmThreads)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    if (!__syncthreads_and(mbar_wait(&mbar, phase))) {
+    if (!__syncthreads_and(mbar_wait(&mbar, phase, wl))) {
       ok = false;
       break;
     }
@@ -1039,6 +1039,13 @@ __global__ void __launch_bounds__(kGemmThreads)
 
 }  // namespace
 
+namespace {
+// The first-wait limit every tensor-core launch of this process passes to its
+// kernel (sfd_set_wait_limit).
+std::atomic<uint32_t> g_host_wait_limit{kSpinLimit};
+uint32_t wait_limit_arg() { return g_host_wait_limit.load(std::memory_order_relaxed); }
+}  // namespace
+
 void cross_gram_tc(const float* X1, int ld1, int n1, const float* X2, int ld2, int n2,
                    int64_t rows, float* G, Workspace& ws, cudaStream_t s) {
   if (n1 < 1 || n1 > 128 || n2 < 0 || n2 > 128)
@@ -1058,7 +1065,7 @@ void cross_gram_tc(const float* X1, int ld1, int n1, const float* X2, int ld2, i
     throw CudaError{cudaErrorInvalidValue, "cross_gram_tc: partial buffer"};
   if (rows > 0) {
     k_tc_cross<<<nchunks, kTcThreads, kXSmem, s>>>(X1, ld1, n1, X2 ? X2 : X1, ld2, n2, rows, rpc,
-                                                   ws.gram_partial, ws.flags);
+                                                   ws.gram_partial, wait_limit_arg(), ws.flags);
     SFD_LAUNCH_CHECK();
   } else {
     nchunks = 0;
@@ -1109,16 +1116,16 @@ void gram_tc(const float* X, int ldx, ColMap map, int64_t rows, float* G, Worksp
   if (rows > 0) {
     if (bulk && split)
       k_tc_gram_bulk<true><<<nchunks, kGramThreads, GramBulk<true>::Smem, s>>>(
-          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+          X, ldx, n, rows, rpc, ws.gram_partial, wait_limit_arg(), ws.flags);
     else if (bulk)
       k_tc_gram_bulk<false><<<nchunks, kGramThreads, GramBulk<false>::Smem, s>>>(
-          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+          X, ldx, n, rows, rpc, ws.gram_partial, wait_limit_arg(), ws.flags);
     else if (split)
       k_tc_gram<true><<<nchunks, kTcThreads, GramRing<true>::Smem, s>>>(
-          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+          X, ldx, n, rows, rpc, ws.gram_partial, wait_limit_arg(), ws.flags);
     else
       k_tc_gram<false><<<nchunks, kTcThreads, GramRing<false>::Smem, s>>>(
-          X, ldx, n, rows, rpc, ws.gram_partial, ws.flags);
+          X, ldx, n, rows, rpc, ws.gram_partial, wait_limit_arg(), ws.flags);
     SFD_LAUNCH_CHECK();
   } else {
     nchunks = 0;
@@ -1155,10 +1162,12 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
     const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
     if (vec)
       k_tc_gemm3<true><<<grid, kGemmThreads, gemm3_smem(n, kout), s>>>(
-          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, ws.flags);
+          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, wait_limit_arg(),
+          ws.flags);
     else
       k_tc_gemm3<false><<<grid, kGemmThreads, gemm3_smem(n, kout), s>>>(
-          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, ws.flags);
+          X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, accumulate, wait_limit_arg(),
+          ws.flags);
     SFD_LAUNCH_CHECK();
     return;
   }
@@ -1188,14 +1197,14 @@ void gemm_ts_tc(const float* X, int ldx, ColMap map, int64_t rows, const float* 
   const bool vec = (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0;
   auto k = vec ? (nb >= 4 ? k_tc_gemm<true, 4> : nb == 3 ? k_tc_gemm<true, 3> : k_tc_gemm<true, 2>)
                : (nb >= 4 ? k_tc_gemm<false, 4> : nb == 3 ? k_tc_gemm<false, 3> : k_tc_gemm<false, 2>);
-  k<<<grid, kGemmThreads, bytes, s>>>(X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, Yh, ws.flags);
+  k<<<grid, kGemmThreads, bytes, s>>>(X, ldx, n, rows, rpc, T, kout, Kp, Np, Y, ldy, Yh,
+                                      wait_limit_arg(), ws.flags);
   SFD_LAUNCH_CHECK();
 }
 
 
 void set_wait_limit(int64_t spins) {
-  const uint32_t v = spins < 0 ? kSpinLimit : (uint32_t)std::min<int64_t>(spins, kSpinLimit);
-  SFD_CUDA(cudaMemcpyToSymbol(g_wait_limit, &v, sizeof(v)));
+  g_host_wait_limit.store(spins < 0 ? kSpinLimit : (uint32_t)std::min<int64_t>(spins, kSpinLimit));
 }
 
 int wait_selftest(int64_t spins, float* ms) {

@@ -154,9 +154,9 @@ void spmv(const Csr& c, const float* x, float* y, float* partial, cudaStream_t s
           const double* xscale = nullptr);
 
 // Bounded waits of the tensor-core stages (failure detection without a GPU
-// fault): set the iteration limit of every stage's first waits on the current
-// device (spins < 0: the default; 0: such a wait gives up at once; call with no
-// library work in flight), and run one wait that nothing ends with the given
+// fault): set the iteration limit of every stage's first waits for the
+// launches that follow, process-wide (spins < 0: the default; 0: such a wait
+// gives up at once), and run one wait that nothing ends with the given
 // limit (returns 1 when it ran out, as it must; *ms: its duration).
 void set_wait_limit(int64_t spins);
 int wait_selftest(int64_t spins, float* ms);
