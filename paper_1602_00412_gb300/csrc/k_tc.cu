@@ -681,7 +681,7 @@ __global__ void k_cross_reduce(const float* __restrict__ partial, int nchunks, i
 // n padded to Kp = 8j, kout to Np = 16j) is staged once per CTA. Each CTA
 // owns one contiguous range of rows_per_cta rows, cut into 128-row tiles
 // that go through NB cp.async buffers: the first NB tiles are all requested
-// before the first MMA (at the C2 shape, 50,000 rows of l = 100 on 152 SMs,
+// before the first MMA (for 50,000 rows of l = 100 on 152 SMs,
 // that is the CTA's whole range), and a buffer takes the tile NB further on
 // once the MMAs that read it have completed. Each tile is multiplied (Kp / 8
 // MMAs) and written back from tensor memory while the later tiles are still

@@ -219,7 +219,7 @@ def c1(seed=0, n=10000):
 
 
 def c1_gapped(seed=0, n=10000):
-    """C1 shape with a planted gap at l=50 (prototype rows)."""
+    """d=2,000 rows of the c1 shape with a planted gap at l=50 (prototype rows)."""
     return gapped(n, 2000, 50, 20, 1.1, seed, name="c1_gapped")
 
 
@@ -239,14 +239,15 @@ def c5(seed=0, n=2_000_000):
 
 
 def c3_chunk(seed, i, n=625_000):
-    """Chunk i of the chunk-parallel C3 stream (8 chunks of 625,000 rows make
-    the 5,000,000-row stream): the C3 row distribution drawn from seed (seed, 3, i)."""
+    """Chunk i of the chunk-parallel bag-of-words stream of c3 (d=200,000; 8
+    chunks of 625,000 rows make its 5,000,000 rows): c3's row distribution
+    drawn from seed (seed, 3, i)."""
     return bow(n, 200000, 4.2, 0.8, 1.05, 2.0, [seed, 3, i], name="c3")
 
 
 def c5_chunk(seed, i, n=500_000):
-    """Chunk i of the C5 stream (4 chunks of 500,000 rows make its 2,000,000
-    rows): planted column factors from `seed`, rows from (seed, 5, i)."""
+    """Chunk i of the c5 stream (d=1,000,000; 4 chunks of 500,000 rows make its
+    2,000,000 rows): planted column factors from `seed`, rows from (seed, 5, i)."""
     return planted(n, 1000000, 80, 1.1, 64, 10.0, 0.9, 0.05, seed, name="c5",
                    row_seed=[seed, 5, i])
 
