@@ -333,11 +333,12 @@ int sfd_gemm_ts(int64_t rows, int32_t n, const float* X, int32_t ldx, const floa
  * raising SFD_ETIMEOUT instead of hanging).
  * sfd_set_wait_limit: the limit of each stage's first waits, process-wide,
  * for every tensor-core launch made after the call: spins < 0 restores the
- * default (2^18 tries, about one second on GB300); 0 makes
- * every such wait give up at once, so the next tensor-core stage reports
- * SFD_ETIMEOUT. The waits that drain a failed stage (its copies and MMAs in
- * flight) always keep the default, so a stage that gave up still leaves
- * nothing running.
+ * default (2^18 tries, about one second on GB300); 0 makes every such wait
+ * give up at once, so the next tensor-core stage reports SFD_ETIMEOUT. The
+ * waits that drain a failed stage (its copies and MMAs in flight) always keep
+ * the default, so a stage that gave up still leaves nothing running. A
+ * one-shot call (sfd_gram, sfd_gemm_ts) that returned SFD_ETIMEOUT may simply
+ * be repeated; a context that did must be destroyed.
  * sfd_wait_selftest: one CTA waits, with limit `spins` (< 0: the default), on
  * an mbarrier that nothing arrives at; returns SFD_ETIMEOUT when the wait ran
  * out (the expected outcome), SFD_OK otherwise; *ms_out (nullable) receives
